@@ -1,0 +1,895 @@
+/*
+ * FP64 CPU oracle for the per-pixel guide pass of
+ *   M. Derevyannykh, "Real-Time Path-Guiding Based on Parametric Mixture
+ *   Models" (arXiv 2112.09728).
+ *
+ * TEST INFRASTRUCTURE ONLY. This is the slow, plain statement of what the
+ * guide pass computes, written in double precision, one pixel at a time, in
+ * the order the paper describes it. Only the test-suite, the smoke check and
+ * the benchmark's CPU-baseline leg may load it. It shares no code, header,
+ * constant table or helper with the CUDA implementation, and it never reads
+ * anything the CUDA implementation produced.
+ *
+ * Where the paper fixes a step, the comment names the section or equation.
+ * Where the paper is silent, the function states the reading it implements.
+ *
+ * Decisions that turn floating-point values into integers (the reprojected
+ * pixel index and the depth/normal acceptance test) are taken in IEEE binary32
+ * with a fixed operation order, because the GPU kernel takes them in binary32.
+ * This file must be compiled with -ffp-contract=off so those expressions are
+ * not fused.
+ *
+ * Parity status per function is recorded beside each one ("pinned by ..." or
+ * "parity unpinned").
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Public structs (mirrored by ctypes in oracle/__init__.py).               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t width, height, spp, k_max;
+    uint32_t seed_lo, seed_hi;
+    double pi_min, pi_max, pi_reinit;
+    double depth_tol, normal_tol, rough_min, sigma2_min, rho_max;
+    double init_mu[2], init_sigma[3];
+} or_config;
+
+typedef struct {
+    int32_t kind;            /* 0 orthographic, 1 pinhole */
+    double origin[3], fwd[3], right[3], up[3];
+    double pixel_size;       /* orthographic: world units per pixel */
+    double tan_half_fov;     /* pinhole: tan of half the vertical field of view */
+} or_camera;
+
+typedef struct {
+    int32_t n_lobes;
+    double dir[8][3], kappa[8], amp[8];
+    double constant;
+    int32_t mask_kind;       /* 0 none, 1 sinusoidal occlusion mask */
+    double mask[4];          /* f1, f2, g, unused */
+} or_field;
+
+/* Per-sample outputs of the sampling step, sample-major [s*HW + i]. */
+typedef struct {
+    double *wx, *wy, *wz;    /* world direction */
+    double *radiance;        /* L_i(x, w) */
+    double *pdf;             /* mixture pdf p_mix(w), solid angle */
+    double *mis;             /* balance-heuristic weight of the drawing strategy */
+    double *estimate;        /* F = L f_r cos / p_mix (0 for an invalid draw) */
+    uint8_t *strategy;       /* 0 BRDF, 1 guide, 2 guide draw outside the square -> BRDF */
+    double *pg, *pb;         /* guide and BRDF pdfs (solid angle) at w */
+    double *ux, *uy;         /* square coordinates used for the guide pdf */
+    double *margin;          /* distance of the sample's own decisions to their thresholds */
+} or_samples;
+
+/* strategy byte: low two bits name the strategy, bit 2 marks a wasted draw
+ * (a GGX reflection below the horizon), which contributes nothing */
+enum { S_BRDF = 0, S_GUIDE = 1, S_FALLBACK = 2, S_INVALID = 4 };
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11): a Feistel-like network of 10 rounds; each      */
+/* round multiplies words 0 and 2 by two odd constants, keeps hi and lo     */
+/* halves, xors the high halves with the other words and the round key;    */
+/* the key is advanced by two Weyl increments between rounds.               */
+/* Pinned by the published known-answer vectors (tests/golden).             */
+/* ------------------------------------------------------------------------ */
+void or_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint64_t mul0 = 0xD2511F53u, mul1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += weyl0; k1 += weyl1; }
+        uint64_t p0 = mul0 * (uint64_t)c0;
+        uint64_t p1 = mul1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void or_philox_many(int64_t n, const uint32_t *ctr, const uint32_t key[2], uint32_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) or_philox(ctr + 4 * i, key, out + 4 * i);
+}
+
+/* 24-bit uniform in [0, 1): top 24 bits of the word times 2^-24 (exact in
+ * binary32 and binary64). */
+static double unif(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
+/* 24-bit uniform in (0, 1], for the logarithm of Box-Muller. */
+static double unif_open0(uint32_t w) { return (double)((w >> 8) + 1u) * (1.0 / 16777216.0); }
+
+/* ------------------------------------------------------------------------ */
+/* Shirley-Chiu concentric map M (Eq. 2, "Shirley and Chiu area preserving  */
+/* mapping"): unit square -> unit disk by concentric squares, then the      */
+/* equal-area lift of the disk to the hemisphere, so dw = 2*pi du dv.       */
+/* Pinned by: round trip, constant Jacobian 2*pi, boundary -> horizon,      */
+/* centre -> pole, moments of the uniform hemisphere.                       */
+/* ------------------------------------------------------------------------ */
+void or_square_to_hemi(const double u[2], double w[3])
+{
+    double a = 2.0 * u[0] - 1.0, b = 2.0 * u[1] - 1.0;
+    double r, phi;
+    if (a == 0.0 && b == 0.0) { w[0] = 0.0; w[1] = 0.0; w[2] = 1.0; return; }
+    if (fabs(a) > fabs(b)) { r = a; phi = (M_PI / 4.0) * (b / a); }
+    else { r = b; phi = M_PI / 2.0 - (M_PI / 4.0) * (a / b); }
+    double dx = r * cos(phi), dy = r * sin(phi);
+    double r2 = r * r;
+    double s = sqrt(2.0 - r2);
+    w[0] = dx * s; w[1] = dy * s; w[2] = 1.0 - r2;
+}
+
+void or_hemi_to_square(const double w[3], double u[2])
+{
+    double z = w[2] < 0.0 ? 0.0 : w[2];
+    double inv = 1.0 / sqrt(1.0 + z);
+    double dx = w[0] * inv, dy = w[1] * inv;
+    double r = sqrt(dx * dx + dy * dy);
+    double a, b;
+    if (r == 0.0) { u[0] = 0.5; u[1] = 0.5; return; }
+    double phi = atan2(dy, dx);
+    if (phi < -M_PI / 4.0) phi += 2.0 * M_PI;
+    if (phi < M_PI / 4.0) { a = r; b = (4.0 / M_PI) * phi * r; }
+    else if (phi < 3.0 * M_PI / 4.0) { b = r; a = -(4.0 / M_PI) * (phi - M_PI / 2.0) * r; }
+    else if (phi < 5.0 * M_PI / 4.0) { a = -r; b = -(4.0 / M_PI) * (phi - M_PI) * r; }
+    else { b = -r; a = (4.0 / M_PI) * (phi - 3.0 * M_PI / 2.0) * r; }
+    u[0] = 0.5 * (a + 1.0); u[1] = 0.5 * (b + 1.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Orthonormal basis around the surface normal. The paper does not fix one; */
+/* this is the branchless construction of Duff et al., "Building an         */
+/* Orthonormal Basis, Revisited" (JCGT 2017).                               */
+/* ------------------------------------------------------------------------ */
+void or_basis(const double n[3], double t[3], double b[3])
+{
+    double sg = copysign(1.0, n[2]);
+    double a = -1.0 / (sg + n[2]);
+    double c = n[0] * n[1] * a;
+    t[0] = 1.0 + sg * n[0] * n[0] * a; t[1] = sg * c; t[2] = -sg * n[0];
+    b[0] = c; b[1] = sg + n[1] * n[1] * a; b[2] = -n[1];
+}
+
+static void to_world(const double n[3], const double l[3], double w[3])
+{
+    double t[3], b[3];
+    or_basis(n, t, b);
+    for (int i = 0; i < 3; ++i) w[i] = l[0] * t[i] + l[1] * b[i] + l[2] * n[i];
+}
+
+static void to_local(const double n[3], const double w[3], double l[3])
+{
+    double t[3], b[3];
+    or_basis(n, t, b);
+    l[0] = w[0] * t[0] + w[1] * t[1] + w[2] * t[2];
+    l[1] = w[0] * b[0] + w[1] * b[1] + w[2] * b[2];
+    l[2] = w[0] * n[0] + w[1] * n[1] + w[2] * n[2];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Normal distribution on the square and its mass Z on [0,1]^2.             */
+/* ------------------------------------------------------------------------ */
+typedef struct { double mx, my, sxx, syy, sxy; } gauss2;
+
+/* N(u; mu, Sigma), plain bivariate normal density. */
+double or_gauss_pdf(const double g5[5], const double u[2])
+{
+    double sxx = g5[2], syy = g5[3], sxy = g5[4];
+    double det = sxx * syy - sxy * sxy;
+    double dx = u[0] - g5[0], dy = u[1] - g5[1];
+    double q = (syy * dx * dx - 2.0 * sxy * dx * dy + sxx * dy * dy) / det;
+    return exp(-0.5 * q) / (2.0 * M_PI * sqrt(det));
+}
+
+typedef double (*fn1)(double x, const void *ctx);
+
+static double simpson_rec(fn1 f, const void *c, double a, double b, double fa, double fm,
+                          double fb, double whole, double eps, int depth)
+{
+    double m = 0.5 * (a + b), lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+    double flm = f(lm, c), frm = f(rm, c);
+    double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
+    double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+    double delta = left + right - whole;
+    if (depth <= 0 || fabs(delta) <= 15.0 * eps) return left + right + delta / 15.0;
+    return simpson_rec(f, c, a, m, fa, flm, fm, left, 0.5 * eps, depth - 1) +
+           simpson_rec(f, c, m, b, fm, frm, fb, right, 0.5 * eps, depth - 1);
+}
+
+/* Adaptive Simpson on [a,b]. */
+static double simpson(fn1 f, const void *c, double a, double b, double eps)
+{
+    if (!(b > a)) return 0.0;
+    double fa = f(a, c), fb = f(b, c), m = 0.5 * (a + b), fm = f(m, c);
+    double whole = (b - a) / 6.0 * (fa + 4.0 * fm + fb);
+    return simpson_rec(f, c, a, b, fa, fm, fb, whole, eps, 40);
+}
+
+/* Integral over [0,1] of a function with a Gaussian-shaped peak of scale s at
+ * c: [c-14s, c+14s] is cut into pieces of width s/2 so the adaptive rule
+ * cannot step over the peak; the rest of [0,1] is integrated in one piece
+ * each side. */
+static double integrate_peaked(fn1 f, const void *ctx, double c, double s)
+{
+    double lo = c - 14.0 * s, hi = c + 14.0 * s;
+    double a = lo < 0.0 ? 0.0 : lo, b = hi > 1.0 ? 1.0 : hi;
+    double total = 0.0;
+    if (a > 0.0) total += simpson(f, ctx, 0.0, a, 1e-16);
+    if (b < 1.0) total += simpson(f, ctx, b, 1.0, 1e-16);
+    if (b > a) {
+        int pieces = (int)ceil((b - a) / (0.5 * s));
+        if (pieces < 1) pieces = 1;
+        if (pieces > 4096) pieces = 4096;
+        double h = (b - a) / pieces;
+        for (int i = 0; i < pieces; ++i)
+            total += simpson(f, ctx, a + i * h, a + (i + 1) * h, 1e-16);
+    }
+    return total;
+}
+
+/* x-marginal density times P(0 <= Y <= 1 | X = x). */
+static double z_integrand(double x, const void *ctx)
+{
+    const gauss2 *g = (const gauss2 *)ctx;
+    double sx = sqrt(g->sxx);
+    double px = exp(-0.5 * (x - g->mx) * (x - g->mx) / g->sxx) / (sqrt(2.0 * M_PI) * sx);
+    double cm = g->my + g->sxy / g->sxx * (x - g->mx);
+    double cs = sqrt(g->syy - g->sxy * g->sxy / g->sxx);
+    double hi = (1.0 - cm) / cs, lo = (0.0 - cm) / cs;
+    double p;
+    if (lo > 0.0) p = 0.5 * (erfc(lo / sqrt(2.0)) - erfc(hi / sqrt(2.0)));
+    else if (hi < 0.0) p = 0.5 * (erfc(-hi / sqrt(2.0)) - erfc(-lo / sqrt(2.0)));
+    else p = 1.0 - 0.5 * erfc(-lo / sqrt(2.0)) - 0.5 * erfc(hi / sqrt(2.0));
+    return px * p;
+}
+
+/* Z = integral over [0,1]^2 of N(u; mu, Sigma): the guide's mass inside the
+ * square (the guide's draws outside it fall back to the BRDF). Written as the
+ * textbook conditioning identity: marginal of X times the conditional
+ * probability of Y, integrated over x by adaptive quadrature.
+ * Pinned by: brute-force 2D midpoint sums, the diagonal-Sigma product of 1D
+ * normal cdfs, the orthant probability 1/4 + asin(rho)/(2 pi). */
+double or_rect_mass(const double g5[5])
+{
+    gauss2 g = {g5[0], g5[1], g5[2], g5[3], g5[4]};
+    return integrate_peaked(z_integrand, &g, g.mx, sqrt(g.sxx));
+}
+
+/* Edge integrals for dZ/dtheta, from differentiating under the integral:
+ *   dZ/dmu_x   = int_0^1 [N(0,y) - N(1,y)] dy
+ *   dZ/ds_xx   = 1/2 int_0^1 [dN/dx(1,y) - dN/dx(0,y)] dy
+ *   dZ/ds_xy   = N(1,1) - N(1,0) - N(0,1) + N(0,0)
+ * (dN/dSigma_ij = 1/2 d2N/dmu_i dmu_j, and dN/dmu = -dN/du). The symmetric
+ * off-diagonal entry is one parameter, so its derivative carries both
+ * off-diagonal slots. Pinned by central finite differences of or_rect_mass. */
+typedef struct { const double *g5; int axis; double fixed; int deriv; } edge_ctx;
+
+static double edge_integrand(double t, const void *ctx)
+{
+    const edge_ctx *e = (const edge_ctx *)ctx;
+    double u[2];
+    if (e->axis == 0) { u[0] = e->fixed; u[1] = t; } else { u[0] = t; u[1] = e->fixed; }
+    double n = or_gauss_pdf(e->g5, u);
+    if (!e->deriv) return n;
+    /* dN/du_axis = -N * (Sigma^-1 (u - mu))_axis */
+    double sxx = e->g5[2], syy = e->g5[3], sxy = e->g5[4];
+    double det = sxx * syy - sxy * sxy;
+    double dx = u[0] - e->g5[0], dy = u[1] - e->g5[1];
+    double ix = (syy * dx - sxy * dy) / det, iy = (-sxy * dx + sxx * dy) / det;
+    return -n * (e->axis == 0 ? ix : iy);
+}
+
+static double edge_integral(const double g5[5], int axis, double fixed, int deriv)
+{
+    /* The density restricted to the edge is Gaussian in t with the
+     * conditional mean and spread of the other coordinate. */
+    double mx = g5[0], my = g5[1], sxx = g5[2], syy = g5[3], sxy = g5[4];
+    double c, s;
+    if (axis == 0) { c = my + sxy / sxx * (fixed - mx); s = sqrt(syy - sxy * sxy / sxx); }
+    else { c = mx + sxy / syy * (fixed - my); s = sqrt(sxx - sxy * sxy / syy); }
+    edge_ctx e = {g5, axis, fixed, deriv};
+    return integrate_peaked(edge_integrand, &e, c, s);
+}
+
+void or_rect_mass_grad(const double g5[5], double out[5])
+{
+    double u00[2] = {0, 0}, u01[2] = {0, 1}, u10[2] = {1, 0}, u11[2] = {1, 1};
+    out[0] = edge_integral(g5, 0, 0.0, 0) - edge_integral(g5, 0, 1.0, 0);
+    out[1] = edge_integral(g5, 1, 0.0, 0) - edge_integral(g5, 1, 1.0, 0);
+    out[2] = 0.5 * (edge_integral(g5, 0, 1.0, 1) - edge_integral(g5, 0, 0.0, 1));
+    out[3] = 0.5 * (edge_integral(g5, 1, 1.0, 1) - edge_integral(g5, 1, 0.0, 1));
+    out[4] = or_gauss_pdf(g5, u11) - or_gauss_pdf(g5, u10) - or_gauss_pdf(g5, u01) +
+             or_gauss_pdf(g5, u00);
+}
+
+void or_rect_mass_many(int64_t n, const double *g5, double *z)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) z[i] = or_rect_mass(g5 + 5 * i);
+}
+
+void or_rect_mass_grad_many(int64_t n, const double *g5, double *dz)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) or_rect_mass_grad(g5 + 5 * i, dz + 5 * i);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Materials (Eq. 1's f_r). The paper does not define its BRDFs; the        */
+/* synthetic scenes use a Lambertian surface (f_r = albedo/pi) and a GGX    */
+/* microfacet surface (Walter et al. 2007: alpha = roughness^2, separable   */
+/* Smith shadowing, Fresnel taken as 1, visible normals not used; the draw  */
+/* picks the half vector with density D(h) cos(theta_h) and reflects the    */
+/* view direction about it). rough < 0 marks a Lambertian pixel.            */
+/* All directions are in the local frame (normal = +z).                     */
+/* ------------------------------------------------------------------------ */
+static double ggx_alpha(double rough) { double a = rough * rough; return a < 1e-4 ? 1e-4 : a; }
+
+static double ggx_d(double a2, double nh)
+{
+    double t = nh * nh * (a2 - 1.0) + 1.0;
+    return a2 / (M_PI * t * t);
+}
+
+static double smith_g1(double a2, double c)
+{
+    return 2.0 * c / (c + sqrt(a2 + (1.0 - a2) * c * c));
+}
+
+/* f_r * cos(theta_i). */
+double or_brdf_cos(double rough, double albedo, const double wo[3], const double wi[3])
+{
+    if (wi[2] <= 0.0 || wo[2] <= 0.0) return 0.0;
+    if (rough < 0.0) return albedo / M_PI * wi[2];
+    double a = ggx_alpha(rough), a2 = a * a;
+    double h[3] = {wo[0] + wi[0], wo[1] + wi[1], wo[2] + wi[2]};
+    double hl = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    double nh = h[2] / hl;
+    return albedo * ggx_d(a2, nh) * smith_g1(a2, wi[2]) * smith_g1(a2, wo[2]) / (4.0 * wo[2]);
+}
+
+/* Density of the BRDF draw at wi (solid angle). */
+double or_brdf_pdf(double rough, const double wo[3], const double wi[3])
+{
+    if (wi[2] <= 0.0) return 0.0;
+    if (rough < 0.0) return wi[2] / M_PI;
+    if (wo[2] <= 0.0) return 0.0;
+    double a = ggx_alpha(rough), a2 = a * a;
+    double h[3] = {wo[0] + wi[0], wo[1] + wi[1], wo[2] + wi[2]};
+    double hl = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    double hn[3] = {h[0] / hl, h[1] / hl, h[2] / hl};
+    double oh = wo[0] * hn[0] + wo[1] * hn[1] + wo[2] * hn[2];
+    if (oh <= 0.0) return 0.0;
+    return ggx_d(a2, hn[2]) * hn[2] / (4.0 * oh);
+}
+
+/* BRDF draw from two uniforms in [0,1). Returns 1 for a draw in the upper
+ * hemisphere, 0 for a wasted draw; *margin receives how far the validity
+ * decision was from its threshold. */
+int or_brdf_sample(double rough, const double wo[3], double x1, double x2, double wi[3],
+                   double *margin)
+{
+    if (rough < 0.0) {
+        /* cosine-weighted: radius sqrt(x1) on the disk, lifted */
+        double r = sqrt(x1), phi = 2.0 * M_PI * x2;
+        wi[0] = r * cos(phi); wi[1] = r * sin(phi); wi[2] = sqrt(1.0 - x1);
+        *margin = 1.0;
+        return 1;
+    }
+    double a = ggx_alpha(rough), a2 = a * a;
+    double den = (1.0 - x1) + a2 * x1;
+    double ct = sqrt((1.0 - x1) / den), st = sqrt(a2 * x1 / den);
+    double phi = 2.0 * M_PI * x2;
+    double h[3] = {st * cos(phi), st * sin(phi), ct};
+    double oh = wo[0] * h[0] + wo[1] * h[1] + wo[2] * h[2];
+    for (int i = 0; i < 3; ++i) wi[i] = 2.0 * oh * h[i] - wo[i];
+    double m1 = oh, m2 = wi[2];
+    *margin = fabs(m1) < fabs(m2) ? fabs(m1) : fabs(m2);
+    return (oh > 0.0 && wi[2] > 0.0) ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Analytic incident radiance, standing in for the traced ray of the path-  */
+/* tracing pass: a sum of normalised von Mises-Fisher lobes                 */
+/*   vMF(w; d, k) = k / (2 pi (1 - exp(-2k))) exp(k (d.w - 1)),             */
+/* optionally times a smooth occlusion mask of the world position and the   */
+/* direction, plus a constant.                                              */
+/* ------------------------------------------------------------------------ */
+double or_radiance(const or_field *f, const double x[3], const double w[3])
+{
+    double s = 0.0;
+    for (int j = 0; j < f->n_lobes; ++j) {
+        double k = f->kappa[j];
+        double dot = f->dir[j][0] * w[0] + f->dir[j][1] * w[1] + f->dir[j][2] * w[2];
+        s += f->amp[j] * k / (2.0 * M_PI * (1.0 - exp(-2.0 * k))) * exp(k * (dot - 1.0));
+    }
+    if (f->mask_kind == 1) {
+        double m = 0.5 + 0.5 * sin(2.0 * M_PI * (f->mask[0] * x[0] + f->mask[2] * w[0])) *
+                             cos(2.0 * M_PI * (f->mask[1] * x[1] + f->mask[2] * w[1]));
+        s *= m;
+    }
+    return s + f->constant;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Camera: primary ray of pixel (x, y); the view direction w_o is the       */
+/* reversed ray and the shading point is origin + depth * dir.              */
+/* ------------------------------------------------------------------------ */
+static void camera_ray(const or_camera *c, int W, int H, int x, int y, double o[3], double d[3])
+{
+    if (c->kind == 0) {
+        double sx = (x + 0.5) * c->pixel_size, sy = (y + 0.5) * c->pixel_size;
+        for (int i = 0; i < 3; ++i) {
+            o[i] = c->origin[i] + sx * c->right[i] + sy * c->up[i];
+            d[i] = c->fwd[i];
+        }
+    } else {
+        double aspect = (double)W / (double)H;
+        double sx = (2.0 * (x + 0.5) / W - 1.0) * c->tan_half_fov * aspect;
+        double sy = (1.0 - 2.0 * (y + 0.5) / H) * c->tan_half_fov;
+        double v[3];
+        for (int i = 0; i < 3; ++i) v[i] = c->fwd[i] + sx * c->right[i] + sy * c->up[i];
+        double l = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int i = 0; i < 3; ++i) { o[i] = c->origin[i]; d[i] = v[i] / l; }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gamma: 8 parameters per pixel (abstract; Sec. 3.1), in the order         */
+/*   E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, I                             */
+/* where [X, Y] = M^-1(w), pi is the guide's mixing weight, k the number of  */
+/* training epochs, and I the running mean of the pixel estimate (the       */
+/* paper's eighth parameter is unnamed; this reading keeps the target mass  */
+/* that normalises the second-moment loss).                                  */
+/* ------------------------------------------------------------------------ */
+enum { G_EX = 0, G_EY, G_EXX, G_EYY, G_EXY, G_PI, G_K, G_I };
+
+/* Mean and regularised covariance of the guide from stored moments:
+ * mean clamped to the square, variances floored, correlation clamped. */
+static void derive_gauss(const or_config *cfg, const double *gm, double g5[5])
+{
+    double ex = gm[G_EX], ey = gm[G_EY];
+    double sxx = gm[G_EXX] - ex * ex, syy = gm[G_EYY] - ey * ey, sxy = gm[G_EXY] - ex * ey;
+    if (sxx < cfg->sigma2_min) sxx = cfg->sigma2_min;
+    if (syy < cfg->sigma2_min) syy = cfg->sigma2_min;
+    double lim = cfg->rho_max * sqrt(sxx * syy);
+    if (sxy > lim) sxy = lim;
+    if (sxy < -lim) sxy = -lim;
+    g5[0] = ex < 0.0 ? 0.0 : (ex > 1.0 ? 1.0 : ex);
+    g5[1] = ey < 0.0 ? 0.0 : (ey > 1.0 ? 1.0 : ey);
+    g5[2] = sxx; g5[3] = syy; g5[4] = sxy;
+}
+
+void or_derive_many(const or_config *cfg, int64_t n, const double *gam, double *g5)
+{
+    for (int64_t i = 0; i < n; ++i) derive_gauss(cfg, gam + 8 * i, g5 + 5 * i);
+}
+
+static void init_gamma(const or_config *cfg, double pi, double *gm)
+{
+    double mx = cfg->init_mu[0], my = cfg->init_mu[1];
+    gm[G_EX] = mx; gm[G_EY] = my;
+    gm[G_EXX] = cfg->init_sigma[0] + mx * mx;
+    gm[G_EYY] = cfg->init_sigma[1] + my * my;
+    gm[G_EXY] = cfg->init_sigma[2] + mx * my;
+    gm[G_PI] = pi; gm[G_K] = 0.0; gm[G_I] = 0.0;
+}
+
+void or_init_gamma(const or_config *cfg, double pi, int64_t n, double *gam)
+{
+    for (int64_t i = 0; i < n; ++i) init_gamma(cfg, pi, gam + 8 * i);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reprojection (Sec. 3.1): fetch last frame's Gamma at the pixel the       */
+/* motion vector points to, nearest neighbour; reject on depth and normal   */
+/* differences (SVGF-style); account for the change of hemisphere frame     */
+/* between the old and the new surface; re-initialise rejected pixels with  */
+/* pi = pi_reinit, k = 0, and mark them to sample from the BRDF alone.      */
+/*                                                                          */
+/* Readings (paper silent): mv = previous minus current screen position in  */
+/* pixels; q = floor(p + 0.5 + mv); accept iff q on screen and              */
+/* |d_prev - d_cur| <= depth_tol * d_cur and n_prev . n_cur >= normal_tol,  */
+/* all evaluated in binary32 in this order. Frame change when the normals   */
+/* differ: the guide's mean direction is carried through the world into the */
+/* new frame (clamped to the horizon), the covariance is kept.              */
+/* ------------------------------------------------------------------------ */
+static void frame_change(const double np_[3], const double nc[3], double *gm)
+{
+    double ex = gm[G_EX], ey = gm[G_EY];
+    double sxx = gm[G_EXX] - ex * ex, syy = gm[G_EYY] - ey * ey, sxy = gm[G_EXY] - ex * ey;
+    double mu[2] = {ex < 0.0 ? 0.0 : (ex > 1.0 ? 1.0 : ex), ey < 0.0 ? 0.0 : (ey > 1.0 ? 1.0 : ey)};
+    double wl[3], ww[3], wn[3], mu2[2];
+    or_square_to_hemi(mu, wl);
+    to_world(np_, wl, ww);
+    to_local(nc, ww, wn);
+    if (wn[2] < 0.0) {
+        double r = sqrt(wn[0] * wn[0] + wn[1] * wn[1]);
+        wn[2] = 0.0;
+        if (r > 0.0) { wn[0] /= r; wn[1] /= r; } else { wn[0] = 1.0; wn[1] = 0.0; }
+    }
+    or_hemi_to_square(wn, mu2);
+    gm[G_EX] = mu2[0]; gm[G_EY] = mu2[1];
+    gm[G_EXX] = sxx + mu2[0] * mu2[0];
+    gm[G_EYY] = syy + mu2[1] * mu2[1];
+    gm[G_EXY] = sxy + mu2[0] * mu2[1];
+}
+
+/* One pixel of the reprojection step. Returns accept; writes q (-1 if off
+ * screen) and the reprojected / re-initialised Gamma. */
+static int reproject_pixel(const or_config *cfg, int x, int y, const float *g0, const float *g1,
+                           const float *g0p, const double *gam_prev, double *out, int32_t *q)
+{
+    int W = cfg->width, H = cfg->height;
+    int64_t i = (int64_t)y * W + x;
+    float mvx = g1[4 * i + 0], mvy = g1[4 * i + 1];
+    volatile float fx = ((float)x + 0.5f) + mvx;
+    volatile float fy = ((float)y + 0.5f) + mvy;
+    int acc = 0;
+    *q = -1;
+    if (fx >= 0.0f && fx < (float)W && fy >= 0.0f && fy < (float)H) {
+        int qx = (int)floorf(fx), qy = (int)floorf(fy);
+        int64_t j = (int64_t)qy * W + qx;
+        *q = (int32_t)j;
+        float dc = g0[4 * i + 3], dp = g0p[4 * j + 3];
+        volatile float dd = dp - dc;
+        volatile float dlim = (float)cfg->depth_tol * dc;
+        volatile float n0 = g0p[4 * j + 0] * g0[4 * i + 0];
+        volatile float n1 = g0p[4 * j + 1] * g0[4 * i + 1];
+        volatile float n2 = g0p[4 * j + 2] * g0[4 * i + 2];
+        volatile float ndot = (n0 + n1) + n2;
+        acc = (fabsf(dd) <= dlim) && (ndot >= (float)cfg->normal_tol);
+        if (acc) {
+            memcpy(out, gam_prev + 8 * j, 8 * sizeof(double));
+            int same = memcmp(&g0p[4 * j], &g0[4 * i], 3 * sizeof(float)) == 0;
+            if (!same) {
+                double np_[3] = {g0p[4 * j], g0p[4 * j + 1], g0p[4 * j + 2]};
+                double nc[3] = {g0[4 * i], g0[4 * i + 1], g0[4 * i + 2]};
+                frame_change(np_, nc, out);
+            }
+        }
+    }
+    if (!acc) init_gamma(cfg, cfg->pi_reinit, out);
+    return acc;
+}
+
+void or_reproject(const or_config *cfg, const float *g0, const float *g1, const float *g0p,
+                  const double *gam_prev, double *gam_out, uint8_t *accept, int32_t *qidx)
+{
+    int W = cfg->width, H = cfg->height;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            accept[i] = (uint8_t)reproject_pixel(cfg, x, y, g0, g1, g0p, gam_prev, gam_out + 8 * i,
+                                                 &qidx[i]);
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Guided sampling, mixture pdf and MIS (Eq. 2, Sec. 3.1).                  */
+/*                                                                          */
+/* D(w) = pi N(M^-1(w); mu, Sigma) + (1 - pi) f_r. The guide draw takes two */
+/* N(0,1) variates by Box-Muller, maps them through the Cholesky factor of  */
+/* Sigma and then through M. Reading (paper silent on the square's edge):   */
+/* a guide draw that lands outside [0,1]^2 is replaced by a BRDF draw, so   */
+/* the density of the procedure is exactly                                   */
+/*   p_mix(w) = pi N(u)/(2 pi) + (1 - pi Z) p_b(w),  u = M^-1(w_local),     */
+/* and the one-sample balance-heuristic MIS estimate is F = f / p_mix.      */
+/* Random numbers: Philox4x32-10, key = seed, counter = (pixel, frame,      */
+/* sample, stream); stream 0 drives the strategy choice and Box-Muller,     */
+/* stream 1 the BRDF draw.                                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double g5[5], chol[3], Z, pi_eff;
+    double n[3], wo_l[3], pos[3];
+    double rough, albedo;
+} pixel_ctx;
+
+static void cholesky(const double g5[5], double c[3])
+{
+    c[0] = sqrt(g5[2]);
+    c[1] = g5[4] / c[0];
+    c[2] = sqrt(g5[3] - c[1] * c[1]);
+}
+
+static void pixel_setup(const or_config *cfg, const or_camera *cam, int x, int y,
+                        const float *g0, const float *g1, const double *gm, int reinit,
+                        pixel_ctx *p)
+{
+    int W = cfg->width, H = cfg->height;
+    int64_t i = (int64_t)y * W + x;
+    double o[3], d[3];
+    camera_ray(cam, W, H, x, y, o, d);
+    double depth = g0[4 * i + 3];
+    double wo[3] = {-d[0], -d[1], -d[2]};
+    for (int k = 0; k < 3; ++k) { p->n[k] = g0[4 * i + k]; p->pos[k] = o[k] + depth * d[k]; }
+    to_local(p->n, wo, p->wo_l);
+    p->rough = g1[4 * i + 2];
+    p->albedo = g1[4 * i + 3];
+    derive_gauss(cfg, gm, p->g5);
+    cholesky(p->g5, p->chol);
+    p->Z = or_rect_mass(p->g5);
+    /* Guiding is off on a re-initialised pixel (Sec. 3.1) and on near-mirror
+     * surfaces (Sec. 5; threshold rough_min is this build's reading). */
+    int gated = reinit || (p->rough >= 0.0 && p->rough < cfg->rough_min);
+    p->pi_eff = gated ? 0.0 : gm[G_PI];
+}
+
+/* Evaluate the pieces of the estimator at a local direction; u is the square
+ * coordinate to use for the guide density (NULL: compute M^-1(wl)). */
+static void eval_local(const or_field *fld, const pixel_ctx *p, const double wl[3],
+                       const double *u_in, double *fcos, double *pg, double *pb, double *pmix,
+                       double *rad, double u_out[2])
+{
+    double ww[3];
+    to_world(p->n, wl, ww);
+    *rad = or_radiance(fld, p->pos, ww);
+    if (wl[2] <= 0.0) {
+        *fcos = 0.0; *pg = 0.0; *pb = 0.0; *pmix = 0.0;
+        u_out[0] = u_out[1] = -1.0;
+        return;
+    }
+    double u[2];
+    if (u_in) { u[0] = u_in[0]; u[1] = u_in[1]; } else or_hemi_to_square(wl, u);
+    u_out[0] = u[0]; u_out[1] = u[1];
+    *fcos = *rad * or_brdf_cos(p->rough, p->albedo, p->wo_l, wl);
+    *pb = or_brdf_pdf(p->rough, p->wo_l, wl);
+    *pg = or_gauss_pdf(p->g5, u) / (2.0 * M_PI);
+    *pmix = p->pi_eff * *pg + (1.0 - p->pi_eff * p->Z) * *pb;
+}
+
+static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_field *fld,
+                         uint32_t frame, int x, int y, const float *g0, const float *g1,
+                         const double *gm, int reinit, or_samples *S, double *img)
+{
+    int W = cfg->width, H = cfg->height, spp = cfg->spp;
+    int64_t i = (int64_t)y * W + x, HW = (int64_t)W * H;
+    pixel_ctx p;
+    pixel_setup(cfg, cam, x, y, g0, g1, gm, reinit, &p);
+    uint32_t key[2] = {cfg->seed_lo, cfg->seed_hi};
+    float pi_dec = (float)p.pi_eff; /* the strategy decision is taken in binary32 */
+    double sum = 0.0;
+    for (int s = 0; s < spp; ++s) {
+        int64_t o = (int64_t)s * HW + i;
+        uint32_t c0[4] = {(uint32_t)i, frame, (uint32_t)s, 0u}, r0[4];
+        uint32_t c1[4] = {(uint32_t)i, frame, (uint32_t)s, 1u}, r1[4];
+        or_philox(c0, key, r0);
+        double zeta = unif(r0[0]);
+        double wl[3], u[2], margin = fabs(zeta - (double)pi_dec);
+        int strat, valid, have_u = 0;
+        if (zeta < (double)pi_dec) {
+            double x1 = unif_open0(r0[1]), x2 = unif(r0[2]);
+            double rr = sqrt(-2.0 * log(x1));
+            double z1 = rr * cos(2.0 * M_PI * x2), z2 = rr * sin(2.0 * M_PI * x2);
+            u[0] = p.g5[0] + p.chol[0] * z1;
+            u[1] = p.g5[1] + p.chol[1] * z1 + p.chol[2] * z2;
+            double m = fmin(fmin(fabs(u[0]), fabs(1.0 - u[0])), fmin(fabs(u[1]), fabs(1.0 - u[1])));
+            if (m < margin) margin = m;
+            if (u[0] >= 0.0 && u[0] <= 1.0 && u[1] >= 0.0 && u[1] <= 1.0) {
+                strat = S_GUIDE;
+                or_square_to_hemi(u, wl);
+                valid = wl[2] > 0.0;
+                have_u = 1;
+            } else {
+                strat = S_FALLBACK;
+                or_philox(c1, key, r1);
+                double mb;
+                valid = or_brdf_sample(p.rough, p.wo_l, unif(r1[0]), unif(r1[1]), wl, &mb);
+                if (mb < margin) margin = mb;
+            }
+        } else {
+            strat = S_BRDF;
+            or_philox(c1, key, r1);
+            double mb;
+            valid = or_brdf_sample(p.rough, p.wo_l, unif(r1[0]), unif(r1[1]), wl, &mb);
+            if (mb < margin) margin = mb;
+        }
+        double fcos = 0, pg = 0, pb = 0, pmix = 0, rad, uo[2] = {-1.0, -1.0};
+        if (valid) {
+            eval_local(fld, &p, wl, have_u ? u : NULL, &fcos, &pg, &pb, &pmix, &rad, uo);
+        } else {
+            double wwi[3];
+            to_world(p.n, wl, wwi);
+            rad = or_radiance(fld, p.pos, wwi);
+            strat |= S_INVALID;
+        }
+        double F = (valid && pmix > 0.0) ? fcos / pmix : 0.0;
+        double mis = 0.0;
+        if (valid && pmix > 0.0)
+            mis = strat == S_GUIDE ? p.pi_eff * pg / pmix : (1.0 - p.pi_eff * p.Z) * pb / pmix;
+        double ww[3];
+        to_world(p.n, wl, ww);
+        if (S->wx) { S->wx[o] = ww[0]; S->wy[o] = ww[1]; S->wz[o] = ww[2]; }
+        if (S->radiance) S->radiance[o] = rad;
+        if (S->pdf) S->pdf[o] = pmix;
+        if (S->mis) S->mis[o] = mis;
+        if (S->estimate) S->estimate[o] = F;
+        if (S->strategy) S->strategy[o] = (uint8_t)strat;
+        if (S->pg) S->pg[o] = pg;
+        if (S->pb) S->pb[o] = pb;
+        if (S->ux) { S->ux[o] = uo[0]; S->uy[o] = uo[1]; }
+        if (S->margin) S->margin[o] = margin;
+        sum += F;
+    }
+    img[i] = sum / spp;
+}
+
+void or_sample(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,
+               const float *g0, const float *g1, const double *gam, const uint8_t *reinit,
+               or_samples *S, double *img)
+{
+    int W = cfg->width, H = cfg->height;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            sample_pixel(cfg, cam, fld, frame, x, y, g0, g1, gam + 8 * i, reinit ? reinit[i] : 0, S,
+                         img);
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Training (Sec. 3.2): weighted online EM from this frame's samples.       */
+/*                                                                          */
+/* Only samples drawn by the BRDF strategy train (Sec. 3.2; using all of    */
+/* them drives pi to 1). For each: weight w = f / p_b (the importance       */
+/* weight of the luminance of L f_r cos under the BRDF draw), E-step        */
+/* posterior gamma = pi N / p_mix. Frame statistics a = sum w gamma,        */
+/* b = sum w, S1 = sum w gamma u, S2 = sum w gamma u u^T.                   */
+/* M-step with temporal filtering by the epoch count k (Sec. 3.2, 4.2):     */
+/*   eta = 1 / (min(k, kMax) + 2)                                           */
+/*   a > 0:  E <- E + eta (S/a - E)            (the five moments)           */
+/*   b > 0:  pi <- clamp(pi + eta (a/b - pi), 0.05, 0.95); k <- min(k+1,kMax)*/
+/*   I <- I + eta (mean F - I)                                              */
+/* ------------------------------------------------------------------------ */
+static void update_pixel(const or_config *cfg, const or_camera *cam, int x, int y,
+                         const float *g0, const float *g1, double *gm, int reinit,
+                         const double *wx, const double *wy, const double *wz,
+                         const double *rad, const double *est, const uint8_t *strat)
+{
+    int W = cfg->width, H = cfg->height, spp = cfg->spp;
+    int64_t i = (int64_t)y * W + x, HW = (int64_t)W * H;
+    pixel_ctx p;
+    pixel_setup(cfg, cam, x, y, g0, g1, gm, reinit, &p);
+    double a = 0, b = 0, s1x = 0, s1y = 0, s2xx = 0, s2yy = 0, s2xy = 0, fsum = 0;
+    for (int s = 0; s < spp; ++s) {
+        int64_t o = (int64_t)s * HW + i;
+        fsum += est[o];
+        if (strat[o] != S_BRDF) continue; /* guide draws, fallbacks and wasted draws do not train */
+        double ww[3] = {wx[o], wy[o], wz[o]}, wl[3];
+        to_local(p.n, ww, wl);
+        if (wl[2] <= 0.0) continue;
+        double u[2];
+        or_hemi_to_square(wl, u);
+        double fcos = rad[o] * or_brdf_cos(p.rough, p.albedo, p.wo_l, wl);
+        double pb = or_brdf_pdf(p.rough, p.wo_l, wl);
+        if (!(pb > 0.0)) continue;
+        double pg = or_gauss_pdf(p.g5, u) / (2.0 * M_PI);
+        double pmix = p.pi_eff * pg + (1.0 - p.pi_eff * p.Z) * pb;
+        double w = fcos / pb;
+        double gam = pmix > 0.0 ? p.pi_eff * pg / pmix : 0.0;
+        a += w * gam; b += w;
+        s1x += w * gam * u[0]; s1y += w * gam * u[1];
+        s2xx += w * gam * u[0] * u[0]; s2yy += w * gam * u[1] * u[1]; s2xy += w * gam * u[0] * u[1];
+    }
+    double k = gm[G_K] < 0.0 ? 0.0 : gm[G_K];
+    double kc = k < cfg->k_max ? k : cfg->k_max;
+    double eta = 1.0 / (kc + 2.0);
+    if (a > 0.0) {
+        gm[G_EX] += eta * (s1x / a - gm[G_EX]);
+        gm[G_EY] += eta * (s1y / a - gm[G_EY]);
+        gm[G_EXX] += eta * (s2xx / a - gm[G_EXX]);
+        gm[G_EYY] += eta * (s2yy / a - gm[G_EYY]);
+        gm[G_EXY] += eta * (s2xy / a - gm[G_EXY]);
+    }
+    if (b > 0.0) {
+        double pi = gm[G_PI] + eta * (a / b - gm[G_PI]);
+        gm[G_PI] = pi < cfg->pi_min ? cfg->pi_min : (pi > cfg->pi_max ? cfg->pi_max : pi);
+        k = k + 1.0;
+        if (k > cfg->k_max) k = cfg->k_max;
+    }
+    gm[G_K] = k;
+    gm[G_I] += eta * (fsum / spp - gm[G_I]);
+}
+
+void or_update(const or_config *cfg, const or_camera *cam, const float *g0, const float *g1,
+               double *gam, const uint8_t *reinit, const double *wx, const double *wy,
+               const double *wz, const double *rad, const double *est, const uint8_t *strat)
+{
+    int W = cfg->width, H = cfg->height;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            update_pixel(cfg, cam, x, y, g0, g1, gam + 8 * i, reinit ? reinit[i] : 0, wx, wy, wz,
+                         rad, est, strat);
+        }
+}
+
+/* One whole frame: reprojection, sampling and training, pixel by pixel.
+ * gam_prev and gam_out are HW x 8; samples S may have NULL planes except the
+ * ones the training step reads (wx, wy, wz, radiance, estimate, strategy). */
+void or_frame(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,
+              const float *g0, const float *g1, const float *g0p, const double *gam_prev,
+              double *gam_out, uint8_t *accept, or_samples *S, double *img)
+{
+    int W = cfg->width, H = cfg->height;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            int32_t q;
+            int acc = reproject_pixel(cfg, x, y, g0, g1, g0p, gam_prev, gam_out + 8 * i, &q);
+            if (accept) accept[i] = (uint8_t)acc;
+            sample_pixel(cfg, cam, fld, frame, x, y, g0, g1, gam_out + 8 * i, !acc, S, img);
+            update_pixel(cfg, cam, x, y, g0, g1, gam_out + 8 * i, !acc, S->wx, S->wy, S->wz,
+                         S->radiance, S->estimate, S->strategy);
+        }
+}
+
+/* Evaluate the mixture at caller-given world directions: for each pixel and
+ * each of n directions, the pieces p_g, p_b, p_mix, the two balance weights,
+ * f_r cos and the radiance. Output layout [k][n*HW + i] for k = 0..6. */
+void or_eval(const or_config *cfg, const or_camera *cam, const or_field *fld, const float *g0,
+             const float *g1, const double *gam, const uint8_t *reinit, int n,
+             const double *dirs /* [n*HW][3] */, double *out)
+{
+    int W = cfg->width, H = cfg->height;
+    int64_t HW = (int64_t)W * H, tot = (int64_t)n * HW;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            pixel_ctx p;
+            pixel_setup(cfg, cam, x, y, g0, g1, gam + 8 * i, reinit ? reinit[i] : 0, &p);
+            for (int s = 0; s < n; ++s) {
+                int64_t o = (int64_t)s * HW + i;
+                double wl[3], fcos, pg, pb, pmix, rad, uo[2];
+                to_local(p.n, dirs + 3 * o, wl);
+                eval_local(fld, &p, wl, NULL, &fcos, &pg, &pb, &pmix, &rad, uo);
+                double wg = pmix > 0 ? p.pi_eff * pg / pmix : 0.0;
+                double wb = pmix > 0 ? (1.0 - p.pi_eff * p.Z) * pb / pmix : 0.0;
+                out[0 * tot + o] = pg;
+                out[1 * tot + o] = pb;
+                out[2 * tot + o] = pmix;
+                out[3 * tot + o] = wg;
+                out[4 * tot + o] = wb;
+                out[5 * tot + o] = fcos;
+                out[6 * tot + o] = rad;
+            }
+        }
+}
+
+/* Per-pixel derived guide: mu, Sigma (regularised), Z, pi_eff. out [HW][8]:
+ * mx, my, sxx, syy, sxy, Z, pi_eff, 0. */
+void or_derive_pixels(const or_config *cfg, const or_camera *cam, const float *g0,
+                      const float *g1, const double *gam, const uint8_t *reinit, double *out)
+{
+    int W = cfg->width, H = cfg->height;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            pixel_ctx p;
+            pixel_setup(cfg, cam, x, y, g0, g1, gam + 8 * i, reinit ? reinit[i] : 0, &p);
+            for (int k = 0; k < 5; ++k) out[8 * i + k] = p.g5[k];
+            out[8 * i + 5] = p.Z; out[8 * i + 6] = p.pi_eff; out[8 * i + 7] = 0.0;
+        }
+}

@@ -1,0 +1,267 @@
+"""Seeded synthetic inputs for the guide pass: G-buffers, cameras, radiance
+fields, guide states and sample sets.
+
+These stand in for the paper's rasterised G-buffer and its Falcor scenes
+(Bistro, Sponza, San Miguel), which are not available; the traced incident
+radiance is replaced by an analytic field of von Mises-Fisher lobes. The module
+holds none of the guide pass's arithmetic: it only draws inputs (numpy, CPU),
+which the tests feed both to the CUDA path and to the oracle.
+
+Layouts (all float32, one row per pixel, row-major y*W + x):
+  g0 [H*W, 4]  normal x, y, z, depth (distance along the primary ray)
+  g1 [H*W, 4]  motion x, y (previous minus current screen position, pixels),
+               roughness (negative = Lambertian), albedo
+  gamma [H*W, 8]  E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, I
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+SEED_BASE = 2112097280
+
+
+@dataclasses.dataclass
+class Camera:
+    kind: int                  # 0 orthographic, 1 pinhole
+    origin: tuple
+    fwd: tuple
+    right: tuple
+    up: tuple
+    pixel_size: float = 1.0    # orthographic: world units per pixel
+    tan_half_fov: float = 0.0  # pinhole: tan(vertical fov / 2)
+
+
+@dataclasses.dataclass
+class Field:
+    dirs: np.ndarray           # [n, 3] unit directions
+    kappas: np.ndarray         # [n]
+    amps: np.ndarray           # [n]
+    constant: float = 0.0
+    mask: tuple | None = None  # (f1, f2, g) of the sinusoidal occlusion mask
+
+
+@dataclasses.dataclass
+class Params:
+    width: int
+    height: int
+    spp: int = 1
+    seed: int = 0
+    k_max: int = 32
+    pi_min: float = 0.05
+    pi_max: float = 0.95
+    pi_reinit: float = 0.05
+    depth_tol: float = 0.1
+    normal_tol: float = 0.9
+    rough_min: float = 0.1
+    sigma2_min: float = 1e-4
+    rho_max: float = 0.9
+    init_mu: tuple = (0.5, 0.5)
+    init_sigma: tuple = (0.1, 0.1, 0.0)
+    init_pi: float = 0.5
+
+
+def unit_hemisphere_dirs(rng, n, zmin=0.0):
+    """Uniform directions on the upper hemisphere (z > zmin)."""
+    z = rng.uniform(zmin, 1.0, n)
+    phi = rng.uniform(0.0, 2.0 * np.pi, n)
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+
+
+def top_down_camera(x0=0.0, y0=0.0, height=100.0, pixel_size=1.0):
+    return Camera(0, (x0, y0, height), (0.0, 0.0, -1.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0),
+                  pixel_size=pixel_size)
+
+
+# ----------------------------------------------------------------------------
+# Workload 1: 64x64, static top-down camera, flat Lambertian, 2 lobes + 0.05.
+# ----------------------------------------------------------------------------
+def flat_scene(width=64, height=64, albedo=0.8, depth=1.0):
+    g0 = np.zeros((height * width, 4), np.float32)
+    g0[:, 2] = 1.0
+    g0[:, 3] = depth
+    g1 = np.zeros((height * width, 4), np.float32)
+    g1[:, 2] = -1.0
+    g1[:, 3] = albedo
+    return g0, g1
+
+
+def two_lobe_field(seed):
+    rng = np.random.default_rng(seed)
+    return Field(dirs=unit_hemisphere_dirs(rng, 2, zmin=0.1), kappas=np.array([20.0, 80.0]),
+                 amps=np.ones(2), constant=0.05)
+
+
+def workload_small(width=64, height=64, spp=1, frames=8):
+    """Plain FP32 guide pass on a 64x64 screen, static camera (zero motion),
+    normals +z, Lambertian albedo 0.8, two normalised vMF lobes (kappa 20 and
+    80, directions drawn from the seed) plus a constant 0.05; the guide starts
+    at mu = (0.5, 0.5), Sigma = 0.1 I, pi = 0.5."""
+    seed = SEED_BASE + 1
+    g0, g1 = flat_scene(width, height)
+    return dict(params=Params(width, height, spp=spp, seed=seed), camera=top_down_camera(
+        pixel_size=1.0 / width), field=two_lobe_field(seed), frames=frames,
+        gbuf=lambda t: (g0, g1, g0))
+
+
+# ----------------------------------------------------------------------------
+# Workload 2: 1920x1080 pan over a heightfield, mixed Lambertian / GGX.
+# ----------------------------------------------------------------------------
+class Heightfield:
+    """Spectral fBm: six octaves of four plane waves each, amplitude halving and
+    frequency doubling per octave; heights and analytic gradients in pixel
+    units of the world texel grid."""
+
+    def __init__(self, seed, amplitude=2.0, period=256.0, octaves=6, waves=4):
+        rng = np.random.default_rng(seed)
+        self.terms = []
+        for o in range(octaves):
+            f = 2.0 * np.pi / period * 2.0 ** o
+            a = amplitude * 0.5 ** o
+            for _ in range(waves):
+                th = rng.uniform(0, 2 * np.pi)
+                self.terms.append((a, f * np.cos(th), f * np.sin(th), rng.uniform(0, 2 * np.pi)))
+
+    def eval(self, X, Y):
+        h = np.zeros_like(X, dtype=np.float64)
+        hx = np.zeros_like(h)
+        hy = np.zeros_like(h)
+        for a, kx, ky, ph in self.terms:
+            arg = kx * X + ky * Y + ph
+            h += a * np.sin(arg)
+            c = a * np.cos(arg)
+            hx += c * kx
+            hy += c * ky
+        return h, hx, hy
+
+
+class PanScene:
+    """Orthographic top-down camera panning +2 texels per frame over a world
+    heightfield; frame t sees world texel (x + 2t, y). Each world texel carries
+    a material drawn from the seed: half Lambertian (albedo 0.8), half GGX with
+    roughness U(0.05, 1). The G-buffer of frame t is a slice of the world
+    arrays, so a texel seen in two frames has bit-identical attributes."""
+
+    def __init__(self, width, height, frames, seed, pan=2, cam_height=100.0,
+                 rough_lo=0.05):
+        self.W, self.H, self.T, self.pan = width, height, frames, pan
+        self.cam_height = cam_height
+        ww = width + pan * max(frames, 1)
+        X, Y = np.meshgrid(np.arange(ww, dtype=np.float64) + 0.5,
+                           np.arange(height, dtype=np.float64) + 0.5)
+        h, hx, hy = Heightfield(seed).eval(X, Y)
+        n = np.stack([-hx, -hy, np.ones_like(h)], axis=-1)
+        n /= np.linalg.norm(n, axis=-1, keepdims=True)
+        rng = np.random.default_rng(seed + 7)
+        lam = rng.random((height, ww)) < 0.5
+        rough = np.where(lam, -1.0, rng.uniform(rough_lo, 1.0, (height, ww)))
+        self.world0 = np.concatenate([n, (cam_height - h)[..., None]], -1).astype(np.float32)
+        self.world1 = np.stack([np.full_like(h, float(pan)), np.zeros_like(h), rough,
+                                np.full_like(h, 0.8)], -1).astype(np.float32)
+
+    def gbuffer(self, t):
+        """(g0, g1, g0_prev) of frame t; frame 0 uses its own G-buffer as the
+        previous one (the motion vectors still point 2 texels right)."""
+        s = self.pan * t
+        g0 = np.ascontiguousarray(self.world0[:, s:s + self.W]).reshape(-1, 4)
+        g1 = np.ascontiguousarray(self.world1[:, s:s + self.W]).reshape(-1, 4)
+        if t == 0:
+            return g0, g1, g0
+        sp = self.pan * (t - 1)
+        g0p = np.ascontiguousarray(self.world0[:, sp:sp + self.W]).reshape(-1, 4)
+        return g0, g1, g0p
+
+    def camera(self, t):
+        return top_down_camera(x0=float(self.pan * t), y0=0.0, height=self.cam_height)
+
+
+def masked_lobe_field(seed, n_lobes=4, kappa_lo=5.0, kappa_hi=500.0, constant=0.0):
+    rng = np.random.default_rng(seed + 11)
+    kap = np.exp(rng.uniform(math.log(kappa_lo), math.log(kappa_hi), n_lobes))
+    return Field(dirs=unit_hemisphere_dirs(rng, n_lobes, zmin=0.05), kappas=kap,
+                 amps=np.ones(n_lobes), constant=constant, mask=(1.0 / 97.0, 1.0 / 131.0, 0.5))
+
+
+def workload_pan(width=1920, height=1080, spp=1, frames=60):
+    """Plain FP32 guide pass at 1920x1080, 1 spp, 60 frames: camera panning
+    2 px/frame over an fBm heightfield with matching motion vectors and depth;
+    half the pixels Lambertian, half GGX with roughness U(0.05, 1); radiance =
+    4 vMF lobes with kappa log-uniform in [5, 500] times a smooth occlusion
+    mask in [0, 1]. The guide starts at mu = (0.5, 0.5), Sigma = 0.1 I, pi = 0.5."""
+    seed = SEED_BASE + 2
+    sc = PanScene(width, height, frames, seed)
+    return dict(params=Params(width, height, spp=spp, seed=seed), camera=sc.camera,
+                field=masked_lobe_field(seed), frames=frames, gbuf=sc.gbuffer, scene=sc)
+
+
+# ----------------------------------------------------------------------------
+# Random guide states, directions and sample sets for unit parity.
+# ----------------------------------------------------------------------------
+def random_gamma(rng, n, k_hi=40, edge_frac=0.1):
+    """Guide states as stored moments, exactly representable in float32:
+    means anywhere in the square (a share exactly on its edges), spreads
+    log-uniform in [0.004, 0.6], correlations in (-0.97, 0.97) (beyond the
+    clamp), a share with a negative variance, pi in [0.05, 0.95], k in
+    [0, k_hi], I in [0, 3]."""
+    mx = rng.uniform(0, 1, n)
+    my = rng.uniform(0, 1, n)
+    e = rng.random(n) < edge_frac
+    mx[e] = rng.choice([0.0, 1.0], e.sum())
+    sx = np.exp(rng.uniform(np.log(0.004), np.log(0.6), n))
+    sy = np.exp(rng.uniform(np.log(0.004), np.log(0.6), n))
+    rho = rng.uniform(-0.97, 0.97, n)
+    exx = sx * sx + mx * mx
+    eyy = sy * sy + my * my
+    exy = rho * sx * sy + mx * my
+    neg = rng.random(n) < 0.03
+    exx[neg] = mx[neg] * mx[neg] - 1e-3
+    g = np.stack([mx, my, exx, eyy, exy, rng.uniform(0.05, 0.95, n),
+                  rng.integers(0, k_hi + 1, n).astype(np.float64), rng.uniform(0, 3, n)], 1)
+    return g.astype(np.float32)
+
+
+def random_normals(rng, n, max_tilt=0.6):
+    """Unit normals within max_tilt radians of +z (float32, renormalised)."""
+    t = rng.uniform(0, max_tilt, n)
+    p = rng.uniform(0, 2 * np.pi, n)
+    v = np.stack([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)], 1)
+    v = v.astype(np.float32)
+    return (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+
+
+def random_gbuffer(rng, width, height, ggx_frac=0.5, rough_lo=0.02, max_tilt=0.6):
+    hw = width * height
+    g0 = np.empty((hw, 4), np.float32)
+    g0[:, :3] = random_normals(rng, hw, max_tilt)
+    g0[:, 3] = rng.uniform(1.0, 10.0, hw)
+    g1 = np.empty((hw, 4), np.float32)
+    g1[:, :2] = 0.0
+    ggx = rng.random(hw) < ggx_frac
+    g1[:, 2] = np.where(ggx, rng.uniform(rough_lo, 1.0, hw), -1.0)
+    g1[:, 3] = rng.uniform(0.2, 1.0, hw)
+    return g0, g1
+
+
+def random_directions(rng, n_per_pixel, hw, below_frac=0.05):
+    """World directions [n, hw, 3], mostly upper hemisphere of +z, a share below."""
+    d = rng.normal(size=(n_per_pixel, hw, 3))
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    d[..., 2] = np.abs(d[..., 2])
+    flip = rng.random((n_per_pixel, hw)) < below_frac
+    d[flip, 2] *= -1.0
+    return d.astype(np.float32)
+
+
+def random_samples(rng, spp, hw):
+    """Sample sets for the training step: directions, radiance, estimates and
+    strategy bytes (0 BRDF, 1 guide, 2 fallback, +4 wasted draw)."""
+    n = spp * hw
+    d = random_directions(rng, spp, hw, below_frac=0.02).reshape(n, 3)
+    strat = rng.choice(np.array([0, 0, 1, 2], np.uint8), n)
+    strat[rng.random(n) < 0.03] |= 4
+    return dict(wx=d[:, 0].copy(), wy=d[:, 1].copy(), wz=d[:, 2].copy(),
+                radiance=rng.uniform(0.0, 5.0, n).astype(np.float32),
+                estimate=rng.uniform(0.0, 3.0, n).astype(np.float32), strategy=strat)
