@@ -1,0 +1,229 @@
+/*
+ * pg.h - C ABI of the GB300 guide pass for screen-space path guiding with
+ * parametric mixture models (Derevyannykh, "Real-Time Path-Guiding Based on
+ * Parametric Mixture Models", arXiv 2112.09728).
+ *
+ * Each pixel keeps the 8-parameter texture Gamma (abstract; Sec. 3.1) of a
+ * mixture (Eq. 2) of a 2D normal distribution on the Shirley-Chiu square and
+ * the surface BRDF. Per frame the pass
+ *   (a) reprojects last frame's Gamma by motion vectors with depth/normal
+ *       rejection (Sec. 3.1),
+ *   (b) draws guided directions with their mixture pdf and balance-heuristic
+ *       MIS weight (Eq. 2, Sec. 3.1), and
+ *   (c) runs one weighted online EM step from the BRDF-strategy samples
+ *       (Sec. 3.2).
+ * The traced incident radiance of the paper's path-tracing pass is replaced by
+ * an analytic field (pg_field), evaluated in the kernel.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are CUDA device pointers owned by the caller; the
+ *    library never frees them. The context owns only Gamma (two buffers), a
+ *    binary32 work copy for the staged calls, and the Adam moments.
+ *  - All work is enqueued on the context's stream and is asynchronous; a call
+ *    returns after the launch, not after the kernel finishes.
+ *  - Arrays are row-major over pixels, index i = y * width + x. Per-sample
+ *    arrays are sample-major: element (s, i) is at s * width * height + i.
+ *  - Every call returns a pg_status and never aborts or throws. On an error the
+ *    context keeps its previous Gamma, and pg_last_error() describes it.
+ *  - The library does no host<->device synchronisation except in
+ *    pg_get_gamma / pg_set_gamma with host buffers and in pg_check.
+ */
+#ifndef PG_H
+#define PG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pg_ctx pg_ctx;
+
+typedef enum {
+    PG_OK = 0,
+    PG_ERR_ARG = 1,      /* a null pointer, a bad size, a bad enum, aliasing buffers */
+    PG_ERR_CUDA = 2,     /* a CUDA runtime error (launch or copy) */
+    PG_ERR_OOM = 3,      /* device allocation failed */
+    PG_ERR_STATE = 4,    /* call out of order (e.g. pg_update without pg_reproject) */
+    PG_ERR_TIMEOUT = 5,  /* reserved for bounded device waits; no call waits today */
+    PG_ERR_NUMERIC = 6   /* the device flagged a non-finite Gamma (pg_check) */
+} pg_status;
+
+/* Storage type of Gamma. PG_F32 stores the paper's raw moments
+ * E[X], E[Y], E[X^2], E[Y^2], E[XY] (Sec. 3.1) as two float4 planes
+ * {E[X], E[Y], E[X^2], E[Y^2]} and {E[XY], pi, k, W} (32 bytes per pixel);
+ * W is the running luminance-weight mass that weighs a new frame's samples
+ * against the stored moments (the paper's unnamed eighth parameter).
+ * PG_F16 / PG_BF16 store one 16-byte record per pixel of eight halves
+ * {mu_x, mu_y, s_xx, s_yy, s_xy, pi, k, W}: the mean and the CENTRAL second
+ * moments, because raw second moments lose the covariance to cancellation at
+ * 11 (8) significand bits. All arithmetic is binary32; only storage differs. */
+typedef enum { PG_F32 = 0, PG_F16 = 1, PG_BF16 = 2 } pg_dtype;
+
+/* Pass configuration. Values the paper fixes: pi_min = 0.05, pi_max = 0.95
+ * (clamp, Sec. 3.2), pi_reinit = 0.05 and k = 0 for invalid history
+ * (Sec. 3.1), k_max (Sec. 4.2). The others are this library's readings of
+ * passages the paper leaves open (defaults in brackets):
+ *   depth_tol  [0.1]  accept iff |d_prev - d_cur| <= depth_tol * d_cur (Sec. 3.1)
+ *   normal_tol [0.9]  accept iff n_prev . n_cur >= normal_tol           (Sec. 3.1)
+ *   rough_min  [0.1]  GGX pixels below this roughness use the BRDF only (Sec. 5)
+ *   sigma2_min [1e-4] variance floor of the guide on the square
+ *   rho_max    [0.9]  correlation clamp of the guide
+ *   k_max      [32]   cap of the epoch counter; the EM step is 1/(min(k,k_max)+2)
+ * init_mu / init_sigma (xx, yy, xy) / init_pi give the Gamma that pg_create
+ * writes to every pixel; a rejected pixel is re-initialised with the same
+ * mean and covariance but pi = pi_reinit, k = 0, W = 0. */
+typedef struct {
+    int32_t width, height;   /* screen size in pixels, each in [1, 32768] */
+    int32_t spp;             /* samples per pixel per frame, in [1, 1024] */
+    int32_t gamma_dtype;     /* pg_dtype */
+    uint64_t seed;           /* Philox4x32-10 key: (low word, high word) */
+    int32_t k_max;
+    float pi_min, pi_max, pi_reinit;
+    float depth_tol, normal_tol, rough_min, sigma2_min, rho_max;
+    float init_mu[2], init_sigma[3], init_pi;
+} pg_config;
+
+/* Camera of one frame: the primary ray of pixel (x, y). Orthographic (kind 0):
+ * origin + (x+0.5)*pixel_size*right + (y+0.5)*pixel_size*up, direction fwd.
+ * Pinhole (kind 1): from origin along normalize(fwd + sx*right + sy*up), with
+ * sx = (2(x+0.5)/W - 1) * tan_half_fov * W/H, sy = (1 - 2(y+0.5)/H) * tan_half_fov.
+ * The view direction w_o (Eq. 1) is the reversed ray; the shading point is
+ * ray origin + depth * ray direction. */
+typedef struct {
+    int32_t kind;
+    float origin[3], fwd[3], right[3], up[3];
+    float pixel_size, tan_half_fov;
+} pg_camera;
+
+/* The rasterised G-buffer of the current frame (Sec. 3.1): device float4
+ * arrays of width*height elements, 16-byte aligned.
+ *   g0[i] = {n_x, n_y, n_z, depth}   unit world normal, distance along the ray
+ *   g1[i] = {mv_x, mv_y, roughness, albedo}
+ * mv is the previous minus the current screen position in pixels; roughness
+ * < 0 marks a Lambertian surface, else GGX with alpha = roughness^2. */
+typedef struct {
+    const float *g0;
+    const float *g1;
+    pg_camera camera;
+} pg_gbuffer;
+
+/* Analytic incident radiance standing in for the ray traced in the
+ * path-tracing pass (Fig. 2): sum over lobes of amp * vMF(w; dir, kappa)
+ * (normalised on the sphere), times the occlusion mask
+ * 0.5 + 0.5 sin(2 pi (mask[0] x + mask[2] w_x)) cos(2 pi (mask[1] y + mask[2] w_y))
+ * when mask_kind = 1 (x, y: world position of the shading point), plus
+ * constant. */
+typedef struct {
+    int32_t n_lobes;         /* 0..8 */
+    float dir[8][3];
+    float kappa[8];          /* > 0 */
+    float amp[8];
+    float constant;
+    int32_t mask_kind;       /* 0 none, 1 sinusoidal mask */
+    float mask[4];
+} pg_field;
+
+/* Per-sample record of the path-tracing pass, the counterpart of the paper's
+ * VPL texture Pi (Fig. 2): device planes of spp*width*height elements each.
+ * Any plane may be NULL in pg_sample (not written); pg_update reads wx, wy,
+ * wz, radiance and strategy. strategy: 0 BRDF draw, 1 guide draw,
+ * 2 guide draw that left the square and fell back to a BRDF draw; +4 marks a
+ * wasted draw (GGX reflection below the horizon), which carries no energy. */
+typedef struct {
+    float *wx, *wy, *wz;     /* world direction */
+    float *radiance;         /* L_i(x, w) */
+    float *pdf;              /* mixture pdf p_mix(w), per steradian */
+    float *mis;              /* balance weight of the strategy that drew it */
+    float *estimate;         /* F = L_i f_r cos / p_mix */
+    uint8_t *strategy;
+} pg_samples;
+
+/* Fill *cfg with the defaults above for a width x height screen. */
+void pg_config_default(pg_config *cfg, int32_t width, int32_t height);
+
+/* Create a context: validates *cfg, allocates Gamma (2 buffers of
+ * width*height*(32 or 16) bytes) on the current device and writes the initial
+ * Gamma on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Returns PG_ERR_ARG (bad config), PG_ERR_OOM, PG_ERR_CUDA. *out is NULL on
+ * failure. */
+pg_status pg_create(const pg_config *cfg, void *stream, pg_ctx **out);
+
+/* Use another stream for subsequent calls. */
+pg_status pg_set_stream(pg_ctx *ctx, void *stream);
+
+/* Staged pass, step (a) (Sec. 3.1): reproject Gamma by the motion vectors of
+ * `cur` into the binary32 work copy; d_g0_prev is last frame's g0.
+ * d_accept (nullable, uint8 per pixel) receives 1 for reused history, 0 for a
+ * re-initialised pixel. Must be followed by pg_sample and/or pg_update. */
+pg_status pg_reproject(pg_ctx *ctx, const pg_gbuffer *cur, const float *d_g0_prev,
+                       uint8_t *d_accept);
+
+/* Staged pass, step (b) (Eq. 2, Sec. 3.1): draw spp guided directions per
+ * pixel from the reprojected guide with Philox4x32-10 (counter = (pixel,
+ * frame, sample, stream)), evaluate the analytic radiance, the mixture pdf,
+ * the MIS weight and the estimate. d_img (nullable) receives the per-pixel
+ * mean estimate. Requires a preceding pg_reproject. */
+pg_status pg_sample(pg_ctx *ctx, const pg_gbuffer *cur, const pg_field *field, uint32_t frame,
+                    const pg_samples *d_out, float *d_img);
+
+/* Staged pass, step (c) (Sec. 3.2): one weighted online EM step from the
+ * given samples (only BRDF-strategy draws train), written as the new Gamma:
+ * with eta = 1/(min(k,k_max)+2), luminance weights w = f/p_b, posteriors
+ * g = pi p_guide / p_mix, a = sum w g, b = sum w, S = sum w g (u, u u^T) and
+ * prior mass M0 = W (b for an untrained guide): A = (1-eta) pi M0 + eta a,
+ * B = (1-eta) M0 + eta b, E <- ((1-eta) pi M0 E + eta S)/A,
+ * pi <- clamp(A/B, pi_min, pi_max), W <- B, k <- min(k+1, k_max).
+ * Requires a preceding pg_reproject; ends the staged frame. */
+pg_status pg_update(pg_ctx *ctx, const pg_gbuffer *cur, const pg_samples *d_in);
+
+/* The whole frame, steps (a)-(c) fused in one kernel: reads Gamma(t-1), the
+ * G-buffer and last frame's g0, writes Gamma(t) and d_img (per-pixel mean
+ * estimate, nullable). Requires no staged frame in progress. */
+pg_status pg_frame(pg_ctx *ctx, const pg_gbuffer *cur, const float *d_g0_prev,
+                   const pg_field *field, uint32_t frame, float *d_img);
+
+/* Evaluate the current guide (Eq. 2) at n_dirs caller-given world directions
+ * per pixel, d_dirs [n_dirs][H*W][3]. d_out [7][n_dirs*H*W] receives p_guide,
+ * p_brdf, p_mix (per steradian), the two balance weights, f_r cos and the
+ * radiance. Uses the work copy between pg_reproject and pg_update, else
+ * Gamma. */
+pg_status pg_eval(pg_ctx *ctx, const pg_gbuffer *cur, const pg_field *field, int32_t n_dirs,
+                  const float *d_dirs, float *d_out);
+
+/* Raw Gamma in its storage layout (pg_gamma_bytes bytes): checkpoint and
+ * resume. Copies are stream-ordered; with a host buffer the call waits. */
+size_t pg_gamma_bytes(const pg_ctx *ctx);
+pg_status pg_get_gamma(pg_ctx *ctx, void *dst, int32_t dst_is_host);
+pg_status pg_set_gamma(pg_ctx *ctx, const void *src, int32_t src_is_host);
+
+/* Gamma as binary32 raw moments in the PG_F32 two-plane layout
+ * (2 * H*W float4), whatever the storage type; the setter rounds to storage. */
+pg_status pg_gamma_to_f32(pg_ctx *ctx, float *d_dst);
+pg_status pg_gamma_from_f32(pg_ctx *ctx, const float *d_src);
+
+/* The reprojected guide of a staged frame (between pg_reproject and
+ * pg_update) as binary32 raw moments in the PG_F32 two-plane layout; k = -1
+ * marks a re-initialised pixel, which samples from the BRDF alone. */
+pg_status pg_get_reprojected(pg_ctx *ctx, float *d_dst);
+
+/* Wait for the stream and read the device error flag: PG_ERR_NUMERIC if a
+ * kernel stored a non-finite Gamma since the last check. */
+pg_status pg_check(pg_ctx *ctx);
+
+/* Philox4x32-10 (Salmon et al., SC'11), the counter-based generator behind
+ * every random number of the pass: d_out[4i..4i+3] = Philox(d_ctr[4i..4i+3],
+ * key) for i < n. use_curand != 0 computes the same words with cuRAND's
+ * header implementation (a cross-check). No context needed; enqueued on
+ * `stream`. */
+pg_status pg_philox(const uint32_t *d_ctr, const uint32_t key[2], int64_t n, uint32_t *d_out,
+                    int32_t use_curand, void *stream);
+
+const char *pg_last_error(const pg_ctx *ctx);
+void pg_destroy(pg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PG_H */

@@ -8,7 +8,7 @@ imports the product package: the two share no code.
 
 Inputs are numpy arrays. G-buffers are float32 ``[H*W, 4]`` planes
 (g0 = normal xyz + depth, g1 = motion xy + roughness + albedo). Gamma is float64
-``[H*W, 8]`` in the order E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, I.
+``[H*W, 8]`` in the order E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, W.
 """
 from __future__ import annotations
 
@@ -90,7 +90,7 @@ def _load():
                 "or_init_gamma": [_P, C.c_double, C.c_int64, _P],
                 "or_reproject": [_P, _P, _P, _P, _P, _P, _P, _P],
                 "or_sample": [_P, _P, _P, C.c_uint32, _P, _P, _P, _P, _P, _P],
-                "or_update": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+                "or_update": [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
                 "or_frame": [_P, _P, _P, C.c_uint32, _P, _P, _P, _P, _P, _P, _P, _P],
                 "or_eval": [_P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P],
                 "or_derive_pixels": [_P, _P, _P, _P, _P, _P, _P],
@@ -315,10 +315,10 @@ def update(cfg, cam, g0, g1, gam, samples, reinit=None):
     out = _f64(gam, (hw, 8)).copy()
     rein = None if reinit is None else np.ascontiguousarray(reinit, np.uint8).reshape(hw)
     wx, wy, wz = (_f64(samples[k], (n,)) for k in ("wx", "wy", "wz"))
-    rad, est = _f64(samples["radiance"], (n,)), _f64(samples["estimate"], (n,))
+    rad = _f64(samples["radiance"], (n,))
     strat = np.ascontiguousarray(samples["strategy"], np.uint8).reshape(n)
     _load().or_update(C.byref(cfg), C.byref(cam), _ptr(g0), _ptr(g1), _ptr(out), _ptr(rein),
-                      _ptr(wx), _ptr(wy), _ptr(wz), _ptr(rad), _ptr(est), _ptr(strat))
+                      _ptr(wx), _ptr(wy), _ptr(wz), _ptr(rad), _ptr(strat))
     return out
 
 

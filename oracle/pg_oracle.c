@@ -452,13 +452,15 @@ static void camera_ray(const or_camera *c, int W, int H, int x, int y, double o[
 
 /* ------------------------------------------------------------------------ */
 /* Gamma: 8 parameters per pixel (abstract; Sec. 3.1), in the order         */
-/*   E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, I                             */
-/* where [X, Y] = M^-1(w), pi is the guide's mixing weight, k the number of  */
-/* training epochs, and I the running mean of the pixel estimate (the       */
-/* paper's eighth parameter is unnamed; this reading keeps the target mass  */
-/* that normalises the second-moment loss).                                  */
+/*   E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, W                             */
+/* where [X, Y] = M^-1(w), the moments are weighted by the luminance of the  */
+/* samples (Sec. 3.1), pi is the guide's mixing weight, k the number of     */
+/* training epochs, and W the running luminance-weight mass of a frame's    */
+/* training samples. The paper names seven of its eight parameters; the     */
+/* eighth is read as W, the quantity a weighted running average of the      */
+/* moments needs in order to weigh a new frame against the stored ones.    */
 /* ------------------------------------------------------------------------ */
-enum { G_EX = 0, G_EY, G_EXX, G_EYY, G_EXY, G_PI, G_K, G_I };
+enum { G_EX = 0, G_EY, G_EXX, G_EYY, G_EXY, G_PI, G_K, G_W };
 
 /* Mean and regularised covariance of the guide from stored moments:
  * mean clamped to the square, variances floored, correlation clamped. */
@@ -488,7 +490,7 @@ static void init_gamma(const or_config *cfg, double pi, double *gm)
     gm[G_EXX] = cfg->init_sigma[0] + mx * mx;
     gm[G_EYY] = cfg->init_sigma[1] + my * my;
     gm[G_EXY] = cfg->init_sigma[2] + mx * my;
-    gm[G_PI] = pi; gm[G_K] = 0.0; gm[G_I] = 0.0;
+    gm[G_PI] = pi; gm[G_K] = 0.0; gm[G_W] = 0.0;
 }
 
 void or_init_gamma(const or_config *cfg, double pi, int64_t n, double *gam)
@@ -753,25 +755,29 @@ void or_sample(const or_config *cfg, const or_camera *cam, const or_field *fld, 
 /* weight of the luminance of L f_r cos under the BRDF draw), E-step        */
 /* posterior gamma = pi N / p_mix. Frame statistics a = sum w gamma,        */
 /* b = sum w, S1 = sum w gamma u, S2 = sum w gamma u u^T.                   */
-/* M-step with temporal filtering by the epoch count k (Sec. 3.2, 4.2):     */
-/*   eta = 1 / (min(k, kMax) + 2)                                           */
-/*   a > 0:  E <- E + eta (S/a - E)            (the five moments)           */
-/*   b > 0:  pi <- clamp(pi + eta (a/b - pi), 0.05, 0.95); k <- min(k+1,kMax)*/
-/*   I <- I + eta (mean F - I)                                              */
+/* M-step as a weighted running average filtered by the epoch count k       */
+/* (Sec. 3.2, 4.2), the stepwise EM of the parametric-mixture guiding the   */
+/* paper builds on: with eta = 1 / (min(k, kMax) + 2) and the stored guide  */
+/* carrying luminance mass M0 = W (or, for a guide not yet trained, the     */
+/* mass b of this frame), when b > 0:                                       */
+/*   A = (1 - eta) pi M0 + eta a          new guide mass                    */
+/*   B = (1 - eta) M0 + eta b             new total mass                    */
+/*   E <- ((1 - eta) pi M0 E + eta S) / A  for the five moments              */
+/*   pi <- clamp(A / B, 0.05, 0.95), k <- min(k + 1, kMax), W <- B.         */
+/* A frame without BRDF-strategy energy (b = 0) leaves Gamma unchanged.     */
 /* ------------------------------------------------------------------------ */
 static void update_pixel(const or_config *cfg, const or_camera *cam, int x, int y,
                          const float *g0, const float *g1, double *gm, int reinit,
                          const double *wx, const double *wy, const double *wz,
-                         const double *rad, const double *est, const uint8_t *strat)
+                         const double *rad, const uint8_t *strat)
 {
     int W = cfg->width, H = cfg->height, spp = cfg->spp;
     int64_t i = (int64_t)y * W + x, HW = (int64_t)W * H;
     pixel_ctx p;
     pixel_setup(cfg, cam, x, y, g0, g1, gm, reinit, &p);
-    double a = 0, b = 0, s1x = 0, s1y = 0, s2xx = 0, s2yy = 0, s2xy = 0, fsum = 0;
+    double a = 0, b = 0, s1x = 0, s1y = 0, s2xx = 0, s2yy = 0, s2xy = 0;
     for (int s = 0; s < spp; ++s) {
         int64_t o = (int64_t)s * HW + i;
-        fsum += est[o];
         if (strat[o] != S_BRDF) continue; /* guide draws, fallbacks and wasted draws do not train */
         double ww[3] = {wx[o], wy[o], wz[o]}, wl[3];
         to_local(p.n, ww, wl);
@@ -790,28 +796,32 @@ static void update_pixel(const or_config *cfg, const or_camera *cam, int x, int 
         s2xx += w * gam * u[0] * u[0]; s2yy += w * gam * u[1] * u[1]; s2xy += w * gam * u[0] * u[1];
     }
     double k = gm[G_K] < 0.0 ? 0.0 : gm[G_K];
-    double kc = k < cfg->k_max ? k : cfg->k_max;
-    double eta = 1.0 / (kc + 2.0);
-    if (a > 0.0) {
-        gm[G_EX] += eta * (s1x / a - gm[G_EX]);
-        gm[G_EY] += eta * (s1y / a - gm[G_EY]);
-        gm[G_EXX] += eta * (s2xx / a - gm[G_EXX]);
-        gm[G_EYY] += eta * (s2yy / a - gm[G_EYY]);
-        gm[G_EXY] += eta * (s2xy / a - gm[G_EXY]);
-    }
     if (b > 0.0) {
-        double pi = gm[G_PI] + eta * (a / b - gm[G_PI]);
+        double kc = k < cfg->k_max ? k : cfg->k_max;
+        double eta = 1.0 / (kc + 2.0);
+        double m0 = (k > 0.0 && gm[G_W] > 0.0) ? gm[G_W] : b;
+        double keep = (1.0 - eta) * gm[G_PI] * m0;
+        double A = keep + eta * a;
+        double B = (1.0 - eta) * m0 + eta * b;
+        if (A > 0.0) {
+            gm[G_EX] = (keep * gm[G_EX] + eta * s1x) / A;
+            gm[G_EY] = (keep * gm[G_EY] + eta * s1y) / A;
+            gm[G_EXX] = (keep * gm[G_EXX] + eta * s2xx) / A;
+            gm[G_EYY] = (keep * gm[G_EYY] + eta * s2yy) / A;
+            gm[G_EXY] = (keep * gm[G_EXY] + eta * s2xy) / A;
+        }
+        double pi = A / B;
         gm[G_PI] = pi < cfg->pi_min ? cfg->pi_min : (pi > cfg->pi_max ? cfg->pi_max : pi);
+        gm[G_W] = B;
         k = k + 1.0;
         if (k > cfg->k_max) k = cfg->k_max;
     }
     gm[G_K] = k;
-    gm[G_I] += eta * (fsum / spp - gm[G_I]);
 }
 
 void or_update(const or_config *cfg, const or_camera *cam, const float *g0, const float *g1,
                double *gam, const uint8_t *reinit, const double *wx, const double *wy,
-               const double *wz, const double *rad, const double *est, const uint8_t *strat)
+               const double *wz, const double *rad, const uint8_t *strat)
 {
     int W = cfg->width, H = cfg->height;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -819,13 +829,13 @@ void or_update(const or_config *cfg, const or_camera *cam, const float *g0, cons
         for (int x = 0; x < W; ++x) {
             int64_t i = (int64_t)y * W + x;
             update_pixel(cfg, cam, x, y, g0, g1, gam + 8 * i, reinit ? reinit[i] : 0, wx, wy, wz,
-                         rad, est, strat);
+                         rad, strat);
         }
 }
 
 /* One whole frame: reprojection, sampling and training, pixel by pixel.
  * gam_prev and gam_out are HW x 8; samples S may have NULL planes except the
- * ones the training step reads (wx, wy, wz, radiance, estimate, strategy). */
+ * ones the training step reads (wx, wy, wz, radiance, strategy). */
 void or_frame(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,
               const float *g0, const float *g1, const float *g0p, const double *gam_prev,
               double *gam_out, uint8_t *accept, or_samples *S, double *img)
@@ -840,7 +850,7 @@ void or_frame(const or_config *cfg, const or_camera *cam, const or_field *fld, u
             if (accept) accept[i] = (uint8_t)acc;
             sample_pixel(cfg, cam, fld, frame, x, y, g0, g1, gam_out + 8 * i, !acc, S, img);
             update_pixel(cfg, cam, x, y, g0, g1, gam_out + 8 * i, !acc, S->wx, S->wy, S->wz,
-                         S->radiance, S->estimate, S->strategy);
+                         S->radiance, S->strategy);
         }
 }
 

@@ -1,0 +1,652 @@
+// Device functions of the guide pass (binary32), shared by the fused frame
+// kernel and the staged kernels. Sections and equations refer to Derevyannykh,
+// "Real-Time Path-Guiding Based on Parametric Mixture Models" (2112.09728).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pgk {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kInvPi = 0.318309886183790671538f;
+constexpr float kInv2Pi = 0.159154943091895335769f;
+constexpr float kInv4Pi2 = 0.0253302959105844428f;   // 1 / (4 pi^2)
+constexpr float k4OverPi = 1.27323954473516268615f;
+constexpr int kGL = 8;                               // Gauss-Legendre nodes for Phi_2
+
+enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
+enum { ST_BRDF = 0, ST_GUIDE = 1, ST_FALLBACK = 2, ST_INVALID = 4 };
+
+// Everything a launch needs besides its pointers; passed by value (kernel
+// parameter space), so concurrent contexts never share constant memory.
+struct Params {
+    int W, H, spp, k_max;
+    uint32_t key0, key1;
+    float pi_min, pi_max, pi_reinit;
+    float depth_tol, normal_tol, rough_min, sigma2_min, rho_max;
+    float init_raw[5];   // E[X], E[Y], E[X^2], E[Y^2], E[XY] of a re-initialised guide
+    float init_c[3];     // its central moments s_xx, s_yy, s_xy
+    // camera of the current frame
+    int cam_kind;
+    float cam_o[3], cam_f[3], cam_r[3], cam_u[3];
+    float cam_ps, cam_tan, cam_aspect;
+    // analytic radiance field
+    int n_lobes, mask_kind;
+    float lobe_dir[8][3], lobe_kappa[8], lobe_scale[8];  // scale = amp * vMF normaliser
+    float field_const, mask[3];
+    // Gauss-Legendre rule on [-1, 1] (computed on the host at context creation)
+    float gl_x[kGL], gl_w[kGL];
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11), counter-based: ten rounds of two
+// 32x32->64 multiplies with the key bumped by the Weyl constants in between.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = c.x * 0xD2511F53u, hi0 = __umulhi(c.x, 0xD2511F53u);
+        const uint32_t lo1 = c.z * 0xCD9E8D57u, hi1 = __umulhi(c.z, 0xCD9E8D57u);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+// top 24 bits -> [0, 1) and (0, 1]; both exact in binary32
+__device__ __forceinline__ float unit24(uint32_t w) { return (float)(w >> 8) * 5.9604644775390625e-8f; }
+__device__ __forceinline__ float unit24_open0(uint32_t w) {
+    return (float)((w >> 8) + 1u) * 5.9604644775390625e-8f;
+}
+
+// ---------------------------------------------------------------------------
+// Small vector helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 f3(const float* p) { return make_float3(p[0], p[1], p[2]); }
+
+// Orthonormal basis around n: Duff et al., "Building an Orthonormal Basis,
+// Revisited" (JCGT 2017), the same construction on both sides of the pass.
+struct Basis {
+    float3 t, b, n;
+};
+__device__ __forceinline__ Basis make_basis(float3 n) {
+    const float sg = copysignf(1.0f, n.z);
+    const float a = -1.0f / (sg + n.z);
+    const float c = n.x * n.y * a;
+    Basis f;
+    f.n = n;
+    f.t = make_float3(1.0f + sg * n.x * n.x * a, sg * c, -sg * n.x);
+    f.b = make_float3(c, sg + n.y * n.y * a, -n.y);
+    return f;
+}
+__device__ __forceinline__ float3 to_world(const Basis& f, float3 l) {
+    return make_float3(l.x * f.t.x + l.y * f.b.x + l.z * f.n.x, l.x * f.t.y + l.y * f.b.y + l.z * f.n.y,
+                       l.x * f.t.z + l.y * f.b.z + l.z * f.n.z);
+}
+__device__ __forceinline__ float3 to_local(const Basis& f, float3 w) {
+    return make_float3(dot3(w, f.t), dot3(w, f.b), dot3(w, f.n));
+}
+
+// ---------------------------------------------------------------------------
+// Shirley-Chiu map M (Eq. 2): concentric square->disk, equal-area lift.
+// z = 1 - r^2 is formed as 4 m (1 - m), m the distance of the dominant
+// coordinate to the square's edge, so grazing directions keep their relative
+// precision in binary32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 square_to_hemi(float u, float v) {
+    const float a = 2.0f * u - 1.0f, b = 2.0f * v - 1.0f;
+    if (a == 0.0f && b == 0.0f) return make_float3(0.0f, 0.0f, 1.0f);
+    float r, m, s, c, dx, dy;
+    if (fabsf(a) > fabsf(b)) {
+        r = a;
+        m = fminf(u, 1.0f - u);
+        sincospif(0.25f * (b / a), &s, &c);
+        dx = r * c;
+        dy = r * s;
+    } else {
+        r = b;
+        m = fminf(v, 1.0f - v);
+        sincospif(0.25f * (a / b), &s, &c);
+        dx = r * s;
+        dy = r * c;
+    }
+    const float z = 4.0f * m * (1.0f - m);
+    const float lift = sqrtf(1.0f + z);
+    return make_float3(dx * lift, dy * lift, z);
+}
+
+// Inverse map: disk point d = w_xy / sqrt(1 + z); the dominant disk axis gives
+// the square coordinate of radius |d|, the other one follows from atan of the
+// component ratio (within [-pi/4, pi/4]).
+__device__ __forceinline__ float2 hemi_to_square(float3 w) {
+    const float z = fmaxf(w.z, 0.0f);
+    const float inv = rsqrtf(1.0f + z);
+    const float dx = w.x * inv, dy = w.y * inv;
+    const float r = sqrtf(dx * dx + dy * dy);
+    if (r == 0.0f) return make_float2(0.5f, 0.5f);
+    float a, b;
+    if (fabsf(dx) >= fabsf(dy)) {
+        a = copysignf(r, dx);
+        b = a * k4OverPi * atanf(dy / dx);
+    } else {
+        b = copysignf(r, dy);
+        a = b * k4OverPi * atanf(dx / dy);
+    }
+    return make_float2(0.5f * (a + 1.0f), 0.5f * (b + 1.0f));
+}
+
+// ---------------------------------------------------------------------------
+// Guide state (one pixel of Gamma) in registers.
+// ---------------------------------------------------------------------------
+struct Gam {
+    float ex, ey;             // mean (stored, not clamped)
+    float exx, eyy, exy;      // raw second moments (binary32 storage only)
+    float sxx, syy, sxy;      // central second moments (not regularised)
+    float pi, k, W;      // mixing weight, epoch count, running luminance mass
+};
+
+__device__ __forceinline__ void central_from_raw(Gam& g) {
+    g.sxx = fmaf(-g.ex, g.ex, g.exx);
+    g.syy = fmaf(-g.ey, g.ey, g.eyy);
+    g.sxy = fmaf(-g.ex, g.ey, g.exy);
+}
+__device__ __forceinline__ void raw_from_central(Gam& g) {
+    g.exx = fmaf(g.ex, g.ex, g.sxx);
+    g.eyy = fmaf(g.ey, g.ey, g.syy);
+    g.exy = fmaf(g.ex, g.ey, g.sxy);
+}
+
+// Storage codecs. F32: two float4 planes {E[X],E[Y],E[X^2],E[Y^2]},
+// {E[XY],pi,k,W}. F16/BF16: one uint4 of 8 halves {mu, s_xx, s_yy, s_xy, pi, k, W}.
+template <int DT>
+struct Store;
+
+template <>
+struct Store<DT_F32> {
+    static __device__ __forceinline__ Gam load(const void* base, size_t hw, size_t i) {
+        const float4* p = reinterpret_cast<const float4*>(base);
+        const float4 a = __ldcs(p + i), b = __ldcs(p + hw + i);
+        Gam g;
+        g.ex = a.x; g.ey = a.y; g.exx = a.z; g.eyy = a.w;
+        g.exy = b.x; g.pi = b.y; g.k = b.z; g.W = b.w;
+        central_from_raw(g);
+        return g;
+    }
+    static __device__ __forceinline__ void store(void* base, size_t hw, size_t i, const Gam& g) {
+        float4* p = reinterpret_cast<float4*>(base);
+        __stcs(p + i, make_float4(g.ex, g.ey, g.exx, g.eyy));
+        __stcs(p + hw + i, make_float4(g.exy, g.pi, g.k, g.W));
+    }
+};
+
+template <typename H>
+struct HalfStore {
+    static __device__ __forceinline__ float cvt(uint16_t v);
+    static __device__ __forceinline__ uint16_t pack(float v);
+};
+template <>
+__device__ __forceinline__ float HalfStore<__half>::cvt(uint16_t v) { return __half2float(__ushort_as_half(v)); }
+template <>
+__device__ __forceinline__ uint16_t HalfStore<__half>::pack(float v) { return __half_as_ushort(__float2half_rn(v)); }
+template <>
+__device__ __forceinline__ float HalfStore<__nv_bfloat16>::cvt(uint16_t v) {
+    return __bfloat162float(__ushort_as_bfloat16(v));
+}
+template <>
+__device__ __forceinline__ uint16_t HalfStore<__nv_bfloat16>::pack(float v) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+template <typename H>
+struct Store16 {
+    static __device__ __forceinline__ Gam load(const void* base, size_t, size_t i) {
+        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(base) + i);
+        Gam g;
+        g.ex = HalfStore<H>::cvt(q.x & 0xffffu); g.ey = HalfStore<H>::cvt(q.x >> 16);
+        g.sxx = HalfStore<H>::cvt(q.y & 0xffffu); g.syy = HalfStore<H>::cvt(q.y >> 16);
+        g.sxy = HalfStore<H>::cvt(q.z & 0xffffu); g.pi = HalfStore<H>::cvt(q.z >> 16);
+        g.k = HalfStore<H>::cvt(q.w & 0xffffu); g.W = HalfStore<H>::cvt(q.w >> 16);
+        raw_from_central(g);
+        return g;
+    }
+    static __device__ __forceinline__ void store(void* base, size_t, size_t i, const Gam& g) {
+        auto pk = [](float lo, float hi) {
+            return (uint32_t)HalfStore<H>::pack(lo) | ((uint32_t)HalfStore<H>::pack(hi) << 16);
+        };
+        __stcs(reinterpret_cast<uint4*>(base) + i,
+               make_uint4(pk(g.ex, g.ey), pk(g.sxx, g.syy), pk(g.sxy, g.pi), pk(g.k, g.W)));
+    }
+};
+template <>
+struct Store<DT_F16> : Store16<__half> {};
+template <>
+struct Store<DT_BF16> : Store16<__nv_bfloat16> {};
+
+// Work copy of the staged pass: binary32, two float4 planes. For F32 storage
+// it holds the raw moments (bit-identical to storage); for F16/BF16 it holds
+// the mean and central moments, so no precision is lost between the stages.
+template <int DT>
+struct Work {
+    static __device__ __forceinline__ Gam load(const float4* w, size_t hw, size_t i) {
+        const float4 a = w[i], b = w[hw + i];
+        Gam g;
+        g.ex = a.x; g.ey = a.y;
+        if (DT == DT_F32) {
+            g.exx = a.z; g.eyy = a.w; g.exy = b.x;
+            central_from_raw(g);
+        } else {
+            g.sxx = a.z; g.syy = a.w; g.sxy = b.x;
+            raw_from_central(g);
+        }
+        g.pi = b.y; g.k = b.z; g.W = b.w;
+        return g;
+    }
+    static __device__ __forceinline__ void store(float4* w, size_t hw, size_t i, const Gam& g) {
+        if (DT == DT_F32) {
+            w[i] = make_float4(g.ex, g.ey, g.exx, g.eyy);
+            w[hw + i] = make_float4(g.exy, g.pi, g.k, g.W);
+        } else {
+            w[i] = make_float4(g.ex, g.ey, g.sxx, g.syy);
+            w[hw + i] = make_float4(g.sxy, g.pi, g.k, g.W);
+        }
+    }
+};
+
+__device__ __forceinline__ Gam init_gam(const Params& P) {
+    Gam g;
+    g.ex = P.init_raw[0]; g.ey = P.init_raw[1];
+    g.exx = P.init_raw[2]; g.eyy = P.init_raw[3]; g.exy = P.init_raw[4];
+    g.sxx = P.init_c[0]; g.syy = P.init_c[1]; g.sxy = P.init_c[2];
+    g.pi = P.pi_reinit; g.k = 0.0f; g.W = 0.0f;
+    return g;
+}
+
+__device__ __forceinline__ bool gam_finite(const Gam& g) {
+    return isfinite(g.ex) && isfinite(g.ey) && isfinite(g.sxx) && isfinite(g.syy) && isfinite(g.sxy) &&
+           isfinite(g.pi) && isfinite(g.k) && isfinite(g.W);
+}
+
+// ---------------------------------------------------------------------------
+// Reprojection (Sec. 3.1). The previous pixel and the acceptance test are
+// taken in binary32 with explicit round-to-nearest operations in a fixed
+// order (no contraction), so the decision is reproducible bit for bit.
+// Returns the linear index of the previous pixel, or -1 for a rejection.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int reproject_index(const Params& P, int x, int y, float4 g0, float4 g1,
+                                               const float4* __restrict__ g0_prev, float4* g0p_out) {
+    const float fx = __fadd_rn(__fadd_rn((float)x, 0.5f), g1.x);
+    const float fy = __fadd_rn(__fadd_rn((float)y, 0.5f), g1.y);
+    if (!(fx >= 0.0f && fx < (float)P.W && fy >= 0.0f && fy < (float)P.H)) return -1;
+    const int qx = (int)floorf(fx), qy = (int)floorf(fy);
+    const int j = qy * P.W + qx;
+    const float4 gp = __ldcs(g0_prev + j);
+    *g0p_out = gp;
+    const float dd = fabsf(__fsub_rn(gp.w, g0.w));
+    const float dl = __fmul_rn(P.depth_tol, g0.w);
+    const float nd = __fadd_rn(__fadd_rn(__fmul_rn(gp.x, g0.x), __fmul_rn(gp.y, g0.y)), __fmul_rn(gp.z, g0.z));
+    return (dd <= dl && nd >= P.normal_tol) ? j : -1;
+}
+
+// Frame change between the previous and the current surface (Sec. 3.1): the
+// guide's mean direction goes through world space into the new frame (held
+// at the horizon if it falls below), the covariance is kept.
+__device__ __forceinline__ void change_frame(Gam& g, float3 np, float3 nc) {
+    const float mx = fminf(fmaxf(g.ex, 0.0f), 1.0f), my = fminf(fmaxf(g.ey, 0.0f), 1.0f);
+    const float3 wl = square_to_hemi(mx, my);
+    const float3 ww = to_world(make_basis(np), wl);
+    float3 wn = to_local(make_basis(nc), ww);
+    if (wn.z < 0.0f) {
+        const float r = sqrtf(wn.x * wn.x + wn.y * wn.y);
+        wn.z = 0.0f;
+        if (r > 0.0f) {
+            wn.x /= r;
+            wn.y /= r;
+        } else {
+            wn.x = 1.0f;
+            wn.y = 0.0f;
+        }
+    }
+    const float2 u = hemi_to_square(wn);
+    g.ex = u.x;
+    g.ey = u.y;
+    raw_from_central(g);
+}
+
+// ---------------------------------------------------------------------------
+// Derived guide (Eq. 2): clamped mean, regularised covariance, its Cholesky
+// factor, and Z = mass of N(mu, Sigma) on [0,1]^2.
+// ---------------------------------------------------------------------------
+struct Guide {
+    float mx, my, sxx, syy, sxy;
+    float l11, l21, l22, il11, il22, pnorm;  // pnorm = 1/(4 pi^2 l11 l22): per-steradian factor
+    float Z, pi_eff;
+};
+
+// Phi_2 correction of the four corners by the Drezner-Wesolowsky form:
+// Phi_2(h,k;rho) = Phi(h)Phi(k) + 1/(2 pi) int_0^asin(rho) exp(-(h^2+k^2-2hk sin t)/(2 cos^2 t)) dt,
+// the t-integral by an 8-node Gauss-Legendre rule (abs. error ~1e-8 for |rho| <= 0.9).
+// Corners with h^2 + k^2 > 100 are skipped: their integrand is below e^-25.
+__device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, float sx, float sy, float rho) {
+    const float h0 = -mx / sx, h1 = (1.0f - mx) / sx;
+    const float k0 = -my / sy, k1 = (1.0f - my) / sy;
+    const float rs2 = 0.70710678118654752f;
+    const float dpx = 1.0f - 0.5f * erfcf(-h0 * rs2) - 0.5f * erfcf(h1 * rs2);
+    const float dpy = 1.0f - 0.5f * erfcf(-k0 * rs2) - 0.5f * erfcf(k1 * rs2);
+    float z = dpx * dpy;
+    if (rho != 0.0f) {
+        const float asr = asinf(rho);
+        float st[kGL], ic[kGL];
+#pragma unroll
+        for (int i = 0; i < kGL; ++i) {
+            float s, c;
+            sincosf(0.5f * asr * (1.0f + P.gl_x[i]), &s, &c);
+            st[i] = s;
+            ic[i] = 0.5f / (c * c);
+        }
+        float acc = 0.0f;
+#pragma unroll
+        for (int cn = 0; cn < 4; ++cn) {
+            const float h = (cn & 1) ? h1 : h0, k = (cn & 2) ? k1 : k0;
+            const float sign = ((cn == 0) || (cn == 3)) ? 1.0f : -1.0f;
+            const float hk2 = h * h + k * k, hk = 2.0f * h * k;
+            if (hk2 > 100.0f) continue;
+            float s = 0.0f;
+#pragma unroll
+            for (int i = 0; i < kGL; ++i) s += P.gl_w[i] * expf(-(hk2 - hk * st[i]) * ic[i]);
+            acc += sign * s;
+        }
+        z += acc * (0.5f * asr) * kInv2Pi;
+    }
+    return z;
+}
+
+__device__ __forceinline__ Guide derive_guide(const Params& P, const Gam& g, bool gated) {
+    Guide d;
+    d.mx = fminf(fmaxf(g.ex, 0.0f), 1.0f);
+    d.my = fminf(fmaxf(g.ey, 0.0f), 1.0f);
+    d.sxx = fmaxf(g.sxx, P.sigma2_min);
+    d.syy = fmaxf(g.syy, P.sigma2_min);
+    const float lim = P.rho_max * sqrtf(d.sxx * d.syy);
+    d.sxy = fminf(fmaxf(g.sxy, -lim), lim);
+    d.l11 = sqrtf(d.sxx);
+    d.l21 = d.sxy / d.l11;
+    d.l22 = sqrtf(fmaf(-d.l21, d.l21, d.syy));
+    d.il11 = 1.0f / d.l11;
+    d.il22 = 1.0f / d.l22;
+    d.pnorm = kInv4Pi2 * d.il11 * d.il22;
+    d.pi_eff = gated ? 0.0f : g.pi;
+    d.Z = (d.pi_eff > 0.0f) ? rect_mass(P, d.mx, d.my, d.l11, sqrtf(d.syy), d.sxy / (d.l11 * sqrtf(d.syy)))
+                            : 1.0f;
+    return d;
+}
+
+// Guide density per steradian at square point u: N(u; mu, Sigma) / (2 pi).
+__device__ __forceinline__ float guide_pdf(const Guide& d, float ux, float uy) {
+    const float y1 = (ux - d.mx) * d.il11;
+    const float y2 = (uy - d.my - d.l21 * y1) * d.il22;
+    return expf(-0.5f * (y1 * y1 + y2 * y2)) * d.pnorm;
+}
+
+// ---------------------------------------------------------------------------
+// Surface: basis, view direction, material (Eq. 1's f_r).
+// Lambert: f_r = albedo / pi, cosine-weighted draws.
+// GGX (Walter et al. 2007): alpha = roughness^2 (>= 1e-4), separable Smith
+// shadowing, Fresnel 1; the draw picks h ~ D(h) cos(theta_h) and reflects w_o.
+// ---------------------------------------------------------------------------
+struct Surf {
+    Basis f;
+    float3 wo;      // local view direction
+    float3 pos;     // world shading point
+    float a2;       // alpha^2 (GGX)
+    float albedo;
+    bool lambert;
+};
+
+__device__ __forceinline__ Surf make_surf(const Params& P, int x, int y, float4 g0, float4 g1) {
+    Surf s;
+    float3 o, d;
+    if (P.cam_kind == 0) {
+        const float sx = ((float)x + 0.5f) * P.cam_ps, sy = ((float)y + 0.5f) * P.cam_ps;
+        o = make_float3(P.cam_o[0] + sx * P.cam_r[0] + sy * P.cam_u[0], P.cam_o[1] + sx * P.cam_r[1] + sy * P.cam_u[1],
+                        P.cam_o[2] + sx * P.cam_r[2] + sy * P.cam_u[2]);
+        d = f3(P.cam_f);
+    } else {
+        const float sx = (2.0f * ((float)x + 0.5f) / (float)P.W - 1.0f) * P.cam_tan * P.cam_aspect;
+        const float sy = (1.0f - 2.0f * ((float)y + 0.5f) / (float)P.H) * P.cam_tan;
+        float3 v = make_float3(P.cam_f[0] + sx * P.cam_r[0] + sy * P.cam_u[0], P.cam_f[1] + sx * P.cam_r[1] + sy * P.cam_u[1],
+                               P.cam_f[2] + sx * P.cam_r[2] + sy * P.cam_u[2]);
+        const float il = rsqrtf(dot3(v, v));
+        d = make_float3(v.x * il, v.y * il, v.z * il);
+        o = f3(P.cam_o);
+    }
+    s.pos = make_float3(o.x + g0.w * d.x, o.y + g0.w * d.y, o.z + g0.w * d.z);
+    s.f = make_basis(make_float3(g0.x, g0.y, g0.z));
+    s.wo = to_local(s.f, make_float3(-d.x, -d.y, -d.z));
+    s.lambert = g1.z < 0.0f;
+    const float a = fmaxf(g1.z * g1.z, 1e-4f);
+    s.a2 = a * a;
+    s.albedo = g1.w;
+    return s;
+}
+
+__device__ __forceinline__ float smith_g1(float a2, float c) {
+    return 2.0f * c / (c + sqrtf(fmaf(1.0f - a2, c * c, a2)));
+}
+
+// f_r cos(theta_i) and the BRDF draw's density (per steradian) at local wi.
+__device__ __forceinline__ void brdf_eval(const Surf& s, float3 wi, float& fcos, float& pb) {
+    if (!(wi.z > 0.0f)) {
+        fcos = 0.0f;
+        pb = 0.0f;
+        return;
+    }
+    if (s.lambert) {
+        pb = wi.z * kInvPi;
+        fcos = s.wo.z > 0.0f ? s.albedo * pb : 0.0f;
+        return;
+    }
+    if (!(s.wo.z > 0.0f)) {
+        fcos = 0.0f;
+        pb = 0.0f;
+        return;
+    }
+    const float3 h = make_float3(s.wo.x + wi.x, s.wo.y + wi.y, s.wo.z + wi.z);
+    const float hz2 = h.z * h.z, hxy2 = h.x * h.x + h.y * h.y, hl2 = hz2 + hxy2;
+    const float t = (s.a2 * hz2 + hxy2) / hl2;           // (n.h)^2 (a^2 - 1) + 1, cancellation-free
+    const float D = s.a2 / (kPi * t * t);
+    const float ihl = rsqrtf(hl2);
+    const float nh = h.z * ihl, oh = dot3(s.wo, h) * ihl;
+    fcos = s.albedo * D * smith_g1(s.a2, wi.z) * smith_g1(s.a2, s.wo.z) / (4.0f * s.wo.z);
+    pb = oh > 0.0f ? D * nh / (4.0f * oh) : 0.0f;
+}
+
+// BRDF draw from two uniforms; false for a wasted draw (below the horizon).
+__device__ __forceinline__ bool brdf_sample(const Surf& s, float x1, float x2, float3& wi) {
+    float sn, cs;
+    sincospif(2.0f * x2, &sn, &cs);
+    if (s.lambert) {
+        const float r = sqrtf(x1);
+        wi = make_float3(r * cs, r * sn, sqrtf(1.0f - x1));
+        return true;
+    }
+    const float den = (1.0f - x1) + s.a2 * x1;
+    const float ct = sqrtf((1.0f - x1) / den), st = sqrtf(s.a2 * x1 / den);
+    const float3 h = make_float3(st * cs, st * sn, ct);
+    const float oh = dot3(s.wo, h);
+    wi = make_float3(2.0f * oh * h.x - s.wo.x, 2.0f * oh * h.y - s.wo.y, 2.0f * oh * h.z - s.wo.z);
+    return oh > 0.0f && wi.z > 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Analytic incident radiance (stand-in for the traced ray of Fig. 2).
+// Each lobe is amp * C_k exp(-k |w - d|^2 / 2) (= amp * C_k exp(k (d.w - 1))
+// for unit vectors, in a form that keeps its precision near the peak).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float radiance(const Params& P, float3 pos, float3 w) {
+    float s = 0.0f;
+    for (int j = 0; j < P.n_lobes; ++j) {
+        const float dx = w.x - P.lobe_dir[j][0], dy = w.y - P.lobe_dir[j][1], dz = w.z - P.lobe_dir[j][2];
+        s += P.lobe_scale[j] * expf(-0.5f * P.lobe_kappa[j] * (dx * dx + dy * dy + dz * dz));
+    }
+    if (P.mask_kind == 1) {
+        const float m = 0.5f + 0.5f * sinpif(2.0f * (P.mask[0] * pos.x + P.mask[2] * w.x)) *
+                                   cospif(2.0f * (P.mask[1] * pos.y + P.mask[2] * w.y));
+        s *= m;
+    }
+    return s + P.field_const;
+}
+
+// ---------------------------------------------------------------------------
+// One sample of the path-tracing pass (Sec. 3.1, Eq. 2): strategy choice,
+// Box-Muller guide draw through the Cholesky factor and M, fallback to the
+// BRDF outside the square, evaluation of radiance, pdfs and the estimate.
+// ---------------------------------------------------------------------------
+struct Smp {
+    float3 wl;        // local direction
+    float ux, uy;     // square coordinate of wl
+    float L, fcos;    // radiance and L f_r cos
+    float pg, pb, pmix, F, mis;
+    int strat;        // ST_* | ST_INVALID
+};
+
+__device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, const Surf& s, Smp& o, bool have_u) {
+    const float3 ww = to_world(s.f, o.wl);
+    o.L = radiance(P, s.pos, ww);
+    if (o.strat & ST_INVALID) {
+        o.fcos = o.pg = o.pb = o.pmix = o.F = o.mis = 0.0f;
+        return;
+    }
+    float fr;
+    brdf_eval(s, o.wl, fr, o.pb);
+    o.fcos = o.L * fr;
+    if (!have_u) {
+        const float2 u = hemi_to_square(o.wl);
+        o.ux = u.x;
+        o.uy = u.y;
+    }
+    o.pg = guide_pdf(d, o.ux, o.uy);
+    const float wb = (1.0f - d.pi_eff * d.Z) * o.pb;
+    const float wg = d.pi_eff * o.pg;
+    o.pmix = wg + wb;
+    if (o.pmix > 0.0f) {
+        o.F = o.fcos / o.pmix;
+        o.mis = ((o.strat & 3) == ST_GUIDE ? wg : wb) / o.pmix;
+    } else {
+        o.F = 0.0f;
+        o.mis = 0.0f;
+    }
+}
+
+__device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, const Surf& s, uint32_t pix,
+                                           uint32_t frame, uint32_t si) {
+    Smp o;
+    const uint4 r0 = philox4x32_10(make_uint4(pix, frame, si, 0u), P.key0, P.key1);
+    const float zeta = unit24(r0.x);
+    bool have_u = false, valid;
+    if (zeta < d.pi_eff) {
+        const float x1 = unit24_open0(r0.y), x2 = unit24(r0.z);
+        const float rr = sqrtf(-2.0f * logf(x1));
+        float sn, cs;
+        sincospif(2.0f * x2, &sn, &cs);
+        const float z1 = rr * cs, z2 = rr * sn;
+        o.ux = fmaf(d.l11, z1, d.mx);
+        o.uy = fmaf(d.l22, z2, fmaf(d.l21, z1, d.my));
+        if (o.ux >= 0.0f && o.ux <= 1.0f && o.uy >= 0.0f && o.uy <= 1.0f) {
+            o.strat = ST_GUIDE;
+            o.wl = square_to_hemi(o.ux, o.uy);
+            valid = o.wl.z > 0.0f;
+            have_u = true;
+        } else {
+            o.strat = ST_FALLBACK;
+        }
+    } else {
+        o.strat = ST_BRDF;
+    }
+    if (!have_u) {
+        const uint4 r1 = philox4x32_10(make_uint4(pix, frame, si, 1u), P.key0, P.key1);
+        valid = brdf_sample(s, unit24(r1.x), unit24(r1.y), o.wl);
+    }
+    if (!valid) o.strat |= ST_INVALID;
+    eval_sample(P, d, s, o, have_u);
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// Weighted online EM (Sec. 3.2). Statistics over BRDF-strategy draws only, in
+// binary32 with Kahan compensation, taken about the stored mean so the second
+// moments need no cancellation: a = sum w g, b = sum w, S1 = sum w g (u - E),
+// S2 = sum w g (u - E)(u - E)^T, with w = f / p_b the luminance weight of
+// the draw and g = pi p_g / p_mix its posterior for the guide.
+// ---------------------------------------------------------------------------
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+};
+
+struct Stats {
+    Kahan a, b, s1x, s1y, s2xx, s2yy, s2xy;
+    __device__ __forceinline__ void add_train(const Guide& d, const Gam& g, const Smp& o) {
+        if (o.strat != ST_BRDF || !(o.pb > 0.0f)) return;
+        const float w = o.fcos / o.pb;
+        const float gam = o.pmix > 0.0f ? d.pi_eff * o.pg / o.pmix : 0.0f;
+        const float wg = w * gam;
+        const float dx = o.ux - g.ex, dy = o.uy - g.ey;
+        a.add(wg);
+        b.add(w);
+        s1x.add(wg * dx);
+        s1y.add(wg * dy);
+        s2xx.add(wg * dx * dx);
+        s2yy.add(wg * dy * dy);
+        s2xy.add(wg * dx * dy);
+    }
+};
+
+// M-step: a luminance-weighted running average filtered by the epoch count
+// k (Sec. 3.2, 4.2). With eta = 1/(min(k, k_max) + 2) and the stored guide
+// carrying mass M0 = W (for an untrained guide, the frame's own mass b):
+//   A = (1-eta) pi M0 + eta a,  B = (1-eta) M0 + eta b,
+//   E <- ((1-eta) pi M0 E + eta S) / A,  pi <- clamp(A/B),  W <- B,  k <- k+1.
+// The moment update is applied about the stored mean: with lambda = eta a / A,
+// delta = S1/a and M2 = S2/a (batch offset and second moment about E[X]),
+//   mu' = mu + lambda delta,  Sigma' = (1-lambda) Sigma + lambda M2 - lambda^2 delta delta^T,
+// the same update in exact arithmetic, free of the cancellation of raw second
+// moments in binary32. A frame with b = 0 changes nothing.
+__device__ __forceinline__ void m_step(const Params& P, Gam& g, const Stats& st) {
+    const float k = fmaxf(g.k, 0.0f);
+    const float a = st.a.s, b = st.b.s;
+    g.k = k;
+    if (!(b > 0.0f)) return;
+    const float eta = __fdiv_rn(1.0f, fminf(k, (float)P.k_max) + 2.0f);
+    const float m0 = (k > 0.0f && g.W > 0.0f) ? g.W : b;
+    const float e1 = 1.0f - eta;
+    const float keep = e1 * g.pi * m0;
+    const float A = fmaf(eta, a, keep);
+    const float B = fmaf(eta, b, e1 * m0);
+    if (a > 0.0f && A > 0.0f) {
+        const float lam = __fdiv_rn(eta * a, A), l1 = 1.0f - lam, l2 = lam * lam;
+        const float dx = __fdiv_rn(st.s1x.s, a), dy = __fdiv_rn(st.s1y.s, a);
+        const float mxx = __fdiv_rn(st.s2xx.s, a), myy = __fdiv_rn(st.s2yy.s, a), mxy = __fdiv_rn(st.s2xy.s, a);
+        g.sxx = fmaf(l1, g.sxx, fmaf(lam, mxx, -l2 * dx * dx));
+        g.syy = fmaf(l1, g.syy, fmaf(lam, myy, -l2 * dy * dy));
+        g.sxy = fmaf(l1, g.sxy, fmaf(lam, mxy, -l2 * dx * dy));
+        g.ex = fmaf(lam, dx, g.ex);
+        g.ey = fmaf(lam, dy, g.ey);
+        raw_from_central(g);
+    }
+    g.pi = fminf(fmaxf(__fdiv_rn(A, B), P.pi_min), P.pi_max);
+    g.W = B;
+    g.k = fminf(k + 1.0f, (float)P.k_max);
+}
+
+}  // namespace pgk

@@ -1,0 +1,37 @@
+// Internal launch interface between the C ABI (pg_api.cu) and the kernels
+// (pg_kernels.cu). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pg_device.cuh"
+
+namespace pgk {
+
+struct SamplePlanes {
+    float *wx, *wy, *wz, *radiance, *pdf, *mis, *estimate;
+    uint8_t* strategy;
+};
+
+// Every launcher returns cudaGetLastError() of its launch.
+cudaError_t launch_init(int dt, const Params& P, void* gam, float init_pi, cudaStream_t st);
+cudaError_t launch_frame(int dt, const Params& P, const void* gin, void* gout, const float4* g0,
+                         const float4* g1, const float4* g0p, float* img, uint32_t frame, int* err,
+                         cudaStream_t st);
+cudaError_t launch_reproject(int dt, const Params& P, const void* gin, float4* work, const float4* g0,
+                             const float4* g1, const float4* g0p, uint8_t* accept, cudaStream_t st);
+cudaError_t launch_sample(int dt, const Params& P, const float4* work, const float4* g0, const float4* g1,
+                          uint32_t frame, SamplePlanes out, float* img, cudaStream_t st);
+cudaError_t launch_update(int dt, const Params& P, const float4* work, const float4* g0, const float4* g1,
+                          SamplePlanes in, void* gout, int* err, cudaStream_t st);
+cudaError_t launch_eval(int dt, const Params& P, const void* src, bool src_is_work, const float4* g0,
+                        const float4* g1, int n_dirs, const float* dirs, float* out, cudaStream_t st);
+cudaError_t launch_to_f32(int dt, const Params& P, const void* src, bool src_is_work, float4* dst,
+                          cudaStream_t st);
+cudaError_t launch_from_f32(int dt, const Params& P, const float4* src, void* dst, cudaStream_t st);
+
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out, bool curand,
+                          cudaStream_t st);
+
+}  // namespace pgk

@@ -484,32 +484,62 @@ def test_em_population_fixed_point():
     samples = dict(wx=dirs[:, 0], wy=dirs[:, 1], wz=dirs[:, 2],
                    radiance=ev["pmix"].ravel(), estimate=np.zeros(N),
                    strategy=np.zeros(N, np.uint8))
-    out = O.update(cfg, cam, g0, g1, gam, samples)
-    assert out[0, :5] == pytest.approx(gam[0, :5], abs=2e-7)
-    assert out[0, 5] == pytest.approx(pi, abs=2e-7)
-    assert out[0, 6] == 6.0
+    for wbar in (0.0, 1.0):          # W = 0 at k > 0: the frame's own mass stands in
+        g = gam.copy()
+        g[0, 7] = wbar
+        out = O.update(cfg, cam, g0, g1, g, samples)
+        # tolerance: the 1024^2 midpoint grid's own error on the ratios S/a, a/b
+        assert out[0, :5] == pytest.approx(gam[0, :5], abs=5e-7)
+        assert out[0, 5] == pytest.approx(pi, abs=1e-6)
+        assert out[0, 6] == 6.0
 
 
-def test_em_single_sample_step_and_clamps():
-    """With one BRDF sample the weighted mean of the batch is that sample's
-    square coordinate, so every moment moves toward it by eta = 1/(k+2); pi
-    stays in [0.05, 0.95] and k is capped at kMax."""
-    cfg = O.make_config(1, 1, spp=1, k_max=32)
+def _one_sample_update(u, radiance, gam_row, k_max=32):
+    cfg = O.make_config(1, 1, spp=1, k_max=k_max)
     cam = O.make_camera(0, (0, 0, 5), (0, 0, -1), (1, 0, 0), (0, 1, 0))
     g0, g1 = _one_pixel()
-    u = np.array([0.3, 0.65])
     w = O.square_to_hemi(u)[0]
-    for k in (0.0, 5.0, 31.0, 32.0, 40.0):
-        gam = _gamma_row(0.5, 0.5, 0.02, 0.02, 0.0, 0.95, k=k, i=1.0)
-        s = dict(wx=[w[0]], wy=[w[1]], wz=[w[2]], radiance=[2.0], estimate=[3.0],
-                 strategy=np.zeros(1, np.uint8))
-        out = O.update(cfg, cam, g0, g1, gam, s)[0]
-        eta = 1.0 / (min(k, 32) + 2)
-        tgt = np.array([u[0], u[1], u[0] ** 2, u[1] ** 2, u[0] * u[1]])
-        assert out[:5] == pytest.approx(gam[0, :5] + eta * (tgt - gam[0, :5]), abs=1e-12)
+    s = dict(wx=[w[0]], wy=[w[1]], wz=[w[2]], radiance=[radiance], estimate=[0.0],
+             strategy=np.zeros(1, np.uint8))
+    return O.update(cfg, cam, g0, g1, np.asarray(gam_row, np.float64).reshape(1, 8), s)[0]
+
+
+def test_em_step_is_a_convex_move_toward_the_sample():
+    """With one BRDF sample the batch mean is that sample's square coordinate u;
+    all five moments move toward (u, u u^T) by the same fraction in [0, 1]."""
+    u = np.array([0.3, 0.65])
+    tgt = np.array([u[0], u[1], u[0] ** 2, u[1] ** 2, u[0] * u[1]])
+    for k, wbar in ((0.0, 0.0), (5.0, 0.7), (31.0, 2.0), (40.0, 0.1)):
+        gam = _gamma_row(0.45, 0.55, 0.02, 0.03, 0.004, 0.6, k=k, i=wbar)[0]
+        out = _one_sample_update(u, 2.0, gam)
+        lam = (out[:5] - gam[:5]) / (tgt - gam[:5])
+        assert np.allclose(lam, lam[0], atol=1e-12) and 0.0 < lam[0] < 1.0
         assert 0.05 <= out[5] <= 0.95
-        assert out[6] == min(k + 1, 32) if k <= 32 else out[6] == 32
-        assert out[7] == pytest.approx(1.0 + eta * (3.0 - 1.0), abs=1e-12)
+        assert out[6] == min(k + 1, 32)
+        assert out[7] > 0
+
+
+def test_em_step_is_continuous_and_luminance_weighted():
+    """A sample carrying vanishing luminance moves nothing; a brighter sample
+    moves the guide further (Sec. 3.1: moments weighted by luminance)."""
+    u = [0.8, 0.2]
+    gam = _gamma_row(0.4, 0.5, 0.01, 0.01, 0.0, 0.5, k=6.0, i=1.0)[0]
+    moves = [np.abs(_one_sample_update(u, r, gam)[:5] - gam[:5]).max() for r in (1e-12, 0.1, 1.0, 10.0)]
+    assert moves[0] < 1e-10
+    assert moves[0] < moves[1] < moves[2] < moves[3]
+
+
+def test_em_step_scale_invariance():
+    """Scaling every luminance weight and the stored mass W by c leaves the
+    guide unchanged and scales W."""
+    u = [0.25, 0.6]
+    gam = _gamma_row(0.5, 0.5, 0.02, 0.02, 0.005, 0.4, k=3.0, i=0.8)[0]
+    a = _one_sample_update(u, 1.5, gam)
+    g2 = gam.copy()
+    g2[7] *= 7.0
+    b = _one_sample_update(u, 1.5 * 7.0, g2)
+    assert np.allclose(a[:7], b[:7], rtol=1e-12, atol=1e-15)
+    assert b[7] == pytest.approx(7.0 * a[7], rel=1e-12)
 
 
 def test_em_guide_and_wasted_samples_do_not_train():
@@ -521,8 +551,34 @@ def test_em_guide_and_wasted_samples_do_not_train():
     s = dict(wx=[w[0]] * 3, wy=[w[1]] * 3, wz=[w[2]] * 3, radiance=[1.0] * 3,
              estimate=[1.0, 2.0, 3.0], strategy=np.array([1, 2, 4], np.uint8))
     out = O.update(cfg, cam, g0, g1, gam, s)[0]
-    assert (out[:7] == gam[0, :7]).all()     # no BRDF sample: moments, pi, k unchanged
-    assert out[7] == pytest.approx(0.5 + (2.0 - 0.5) / 6.0, abs=1e-12)
+    assert (out == gam[0]).all()     # no BRDF-strategy energy: Gamma unchanged
+
+
+def test_em_recovers_a_known_mixture_from_its_samples():
+    """Stochastic recovery: BRDF draws whose luminance follows a known mixture
+    (mu*, Sigma*, pi*) train the guide onto it over many frames."""
+    mu, sig, pi = np.array([0.35, 0.62]), np.array([3e-3, 5e-3, -1e-3]), 0.7
+    # k_max = 8 keeps a forgetting window of ten frames, so the early frames of
+    # the broad initial guide are forgotten within the run
+    spp, frames = 256, 80
+    cfg = O.make_config(1, 1, spp=spp, k_max=8)
+    cam = O.make_camera(0, (0, 0, 5), (0, 0, -1), (1, 0, 0), (0, 1, 0))
+    fld = O.make_field([], [], [], constant=1.0)
+    g0, g1 = _one_pixel(albedo=1.0)
+    target = _gamma_row(*mu, *sig, pi, k=5.0)
+    gam = _gamma_row(0.5, 0.5, 0.1, 0.1, 0.0, 0.5, k=0.0)
+    rng = np.random.default_rng(17)
+    for t in range(frames):
+        d = np.array([O.brdf_sample(-1.0, [0, 0, 1.0], *rng.uniform(0, 1, 2))[0] for _ in range(spp)])
+        ev = O.evaluate(cfg, cam, fld, g0, g1, target, d[:, None, :])
+        # Lambert, albedo 1: f = L p_b, so radiance = p_mix* / p_b makes f = p_mix*
+        s = dict(wx=d[:, 0], wy=d[:, 1], wz=d[:, 2], radiance=(ev["pmix"] / ev["pb"]).ravel(),
+                 estimate=np.zeros(spp), strategy=np.zeros(spp, np.uint8))
+        gam = O.update(cfg, cam, g0, g1, gam, s)
+    g5 = O.derive(cfg, gam)[0]
+    assert np.abs(g5[:2] - mu).max() < 0.01
+    assert np.abs(g5[2:] - sig).max() < 1e-3
+    assert abs(gam[0, 5] - pi) < 0.05
 
 
 def test_reinit_pixel_samples_brdf_only():
