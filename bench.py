@@ -1,0 +1,405 @@
+"""Benchmark of the fused guide pass on the 1920x1080 panning workload.
+
+One step = one frame of the whole pass (reprojection, guided sampling with
+MIS, one weighted online EM step) over the full screen: one launch of the
+fused kernel. Default: frames 0-4 warm up, frames 5-59 are timed, i.e. the
+60-frame workload. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Guide-pass Mpix/s @1080p (FP16-Γ vs FP32 plain) at matched MSE; % HBM peak"
+WORKLOAD = ("1920x1080, 1 spp, 60 frames: orthographic camera panning 2 px/frame over a 6-octave fBm "
+            "heightfield (normals, depth and motion vectors from it), 50% Lambert albedo 0.8 / 50% GGX "
+            "roughness U(0.05,1), radiance = 4 vMF lobes kappa log-uniform [5,500] x smooth occlusion mask")
+# algorithmic bytes per pixel of one fused frame: reads Gamma(t-1), g0, g1, g0(t-1); writes Gamma(t), image
+BYTES_PER_PIXEL = {"f32": (32 + 16 + 16 + 16) + (32 + 4), "f16": (16 + 16 + 16 + 16) + (16 + 4),
+                   "bf16": (16 + 16 + 16 + 16) + (16 + 4)}
+MSE_FRAMES = range(30, 60)
+REF_SPP = 256
+
+
+def kernel_traffic():
+    """DRAM bytes per k_frame<F16> launch from the committed ncu summary, or None
+    when the kernel sources changed since those counters were taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "k_frame_1080p_pan.md")
+    src = os.path.join(ROOT, "paper_2112_09728_gb300", "csrc")
+    try:
+        h = hashlib.sha256()
+        for f in ("pg_device.cuh", "pg_kernels.cu", "pg_launch.h"):
+            with open(os.path.join(src, f), "rb") as fh:
+                h.update(fh.read())
+        sha, traffic = None, None
+        with open(prof) as fh:
+            for line in fh:
+                if line.startswith("kernel sources sha256"):
+                    sha = line.split(":")[1].strip()
+                elif line.startswith("traffic_bytes_per_launch:"):
+                    traffic = float(line.split(":")[1])
+        return traffic if sha == h.hexdigest() else None
+    except Exception:
+        return None
+
+
+def measured_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
+    if args.impl != "reference" and torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded strip of the same workload
+# ----------------------------------------------------------------------------
+def oracle_strip_frames(rows, budget_s, min_steps=1, max_steps=1000, frame_base=1):
+    """Run the FP64 oracle on 1920 x rows strips of the workload (frame_base,
+    frame_base+1, ...) until budget_s seconds of work; returns (pixels, seconds, steps)."""
+    import oracle as O
+    from paper_2112_09728_gb300 import scenes
+    wl = scenes.workload_pan(1920, rows, frames=frame_base + max_steps + 1)
+    par, fld, sc = wl["params"], wl["field"], wl["scene"]
+    cfg = O.make_config(par.width, par.height, spp=1, seed=par.seed, init_mu=par.init_mu,
+                        init_sigma=par.init_sigma)
+    of = O.make_field(np.asarray(fld.dirs, np.float32).astype(np.float64), np.float32(fld.kappas).astype(float),
+                      np.float32(fld.amps).astype(float), float(np.float32(fld.constant)),
+                      [float(np.float32(m)) for m in fld.mask])
+    gam = O.init_gamma(cfg, par.width * par.height, pi=par.init_pi)
+    px, sec, steps = 0, 0.0, 0
+    while steps < max_steps and (sec < budget_s or steps < min_steps):
+        t = frame_base + steps
+        g0, g1, g0p = sc.gbuffer(t)
+        cam = sc.camera(t)
+        oc = O.make_camera(cam.kind, cam.origin, cam.fwd, cam.right, cam.up, cam.pixel_size, cam.tan_half_fov)
+        t0 = time.perf_counter()
+        gam, _, _, _ = O.frame(cfg, oc, of, t, g0, g1, g0p, gam)
+        sec += time.perf_counter() - t0
+        px += par.width * par.height
+        steps += 1
+    return px, sec, steps
+
+
+def cpu_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    rows = 8
+    for _ in range(args.warmup):
+        oracle_strip_frames(rows, 0.0, max_steps=1)
+    px, sec, steps = oracle_strip_frames(rows, 0.0, min_steps=args.steps, max_steps=args.steps)
+    v = px / sec / 1e6
+    sample = "%d frames of a 1920x%d strip of the workload (the pan stays within rows)" % (steps, rows)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gamma_storage": "f64", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def upload_frames(sc, n_frames, pin=False):
+    import torch
+    hw = sc.W * sc.H
+    g0 = torch.empty((n_frames, hw, 4), dtype=torch.float32, pin_memory=pin)
+    g1 = torch.empty((n_frames, hw, 4), dtype=torch.float32, pin_memory=pin)
+    for t in range(n_frames):
+        a, b, _ = sc.gbuffer(t)
+        g0[t].copy_(torch.from_numpy(a))
+        g1[t].copy_(torch.from_numpy(b))
+    return g0, g1
+
+
+def make_pass(par, gamma_dtype, seed_offset=0, spp=1):
+    from paper_2112_09728_gb300.guide import GuidePass
+    return GuidePass(par.width, par.height, spp=spp, gamma_dtype=gamma_dtype, seed=par.seed + seed_offset,
+                     init_pi=par.init_pi)
+
+
+def run_form(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush, keep_frames, seed_offset):
+    """Run frames 0..warmup+steps-1; time each of the last `steps` with CUDA events
+    (L2 flushed before each). Returns (per-step ms list, {frame: image})."""
+    import torch
+    gp = make_pass(par, gamma_dtype, seed_offset)
+    hw = par.width * par.height
+    img = torch.empty(hw, dtype=torch.float32, device="cuda")
+    kept = {}
+    ev = []
+    for t in range(warmup + steps):
+        prev = max(t - 1, 0)
+        timed = t >= warmup
+        if timed:
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+        gp.pg_frame(g0d[t], g1d[t], sc.camera(t), g0d[prev], fld, t, img)
+        if timed:
+            e1.record()
+            ev.append((e0, e1))
+        if t in keep_frames:
+            kept[t] = img.clone()
+    torch.cuda.synchronize()
+    gp.pg_check()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    gp.close()
+    return ms, kept
+
+
+def reference_images(par, sc, fld, g0d, g1d, frames):
+    """256-spp estimates of the same frames by the sampling kernel (own seed,
+    broad initial guide): the reference the 1-spp images' MSE is taken against."""
+    import torch
+    out = {}
+    hw = par.width * par.height
+    for t in frames:
+        gp = make_pass(par, "f32", seed_offset=977, spp=REF_SPP)
+        img = torch.empty(hw, dtype=torch.float32, device="cuda")
+        gp.pg_reproject(g0d[t], g1d[t], sc.camera(t), g0d[t])
+        gp.pg_sample(g0d[t], g1d[t], sc.camera(t), fld, 1000003 + t, None, img)
+        out[t] = img
+        torch.cuda.synchronize()
+        gp.close()
+    return out
+
+
+def run_e2e(par, sc, fld, g0h, g1h, gamma_dtype, warmup, steps):
+    """The same frames through the public API from pinned host buffers: every
+    step copies its G-buffer host->device, runs the pass and reads the image
+    back, all inside the timed region."""
+    import torch
+    gp = make_pass(par, gamma_dtype)
+    hw = par.width * par.height
+    g0d = [torch.empty((hw, 4), device="cuda") for _ in range(2)]
+    g1d = torch.empty((hw, 4), device="cuda")
+    img = torch.empty(hw, device="cuda")
+    img_h = torch.empty(hw, pin_memory=True)
+    ms = []
+    for t in range(warmup + steps):
+        cur, prv = g0d[t % 2], g0d[(t - 1) % 2] if t > 0 else g0d[0]
+        timed = t >= warmup
+        if timed:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+        cur.copy_(g0h[t], non_blocking=True)
+        g1d.copy_(g1h[t], non_blocking=True)
+        gp.pg_frame(cur, g1d, sc.camera(t), prv if t > 0 else cur, fld, t, img)
+        img_h.copy_(img, non_blocking=True)
+        if timed:
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    gp.close()
+    return ms, 2 * hw * 16, hw * 4
+
+
+def run_gpu(args, ws, rank, local):
+    import torch
+    from paper_2112_09728_gb300 import scenes
+    import __graft_entry__
+    __graft_entry__.build()
+
+    n_frames = args.warmup + args.steps
+    wl = scenes.workload_pan(1920, 1080, frames=n_frames)
+    par, fld, sc = wl["params"], wl["field"], wl["scene"]
+    hw = par.width * par.height
+    g0h, g1h = upload_frames(sc, n_frames, pin=True)
+    g0d, g1d = g0h.cuda(), g1h.cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB of L2
+    keep = set(t for t in MSE_FRAMES if t < n_frames)
+    torch.cuda.synchronize()
+
+    forms = {}
+    barrier(ws)
+    with ClockSampler(local) as clk:
+        for dt in ("f32", "f16"):
+            ms, kept = run_form(par, sc, fld, g0d, g1d, dt, args.warmup, args.steps, flush, keep, rank)
+            forms[dt] = (ms, kept)
+    barrier(ws)
+    clocks = clk.summary()
+
+    # matched MSE against a 256-spp reference of frames 30-59
+    mse = None
+    if keep:
+        ref = reference_images(par, sc, fld, g0d, g1d, sorted(keep))
+        m = {}
+        for dt in ("f32", "f16"):
+            acc = 0.0
+            for t in sorted(keep):
+                d = (forms[dt][1][t].double() - ref[t].double())
+                acc += float((d * d).mean())
+            m[dt] = acc / len(keep)
+        mse = {"frames": [min(keep), max(keep)], "reference": "%d spp" % REF_SPP, "fp32": m["f32"],
+               "fp16": m["f16"], "ratio_fp16_over_fp32": m["f16"] / m["f32"],
+               "matched": bool(m["f16"] <= 1.02 * m["f32"])}
+
+    e2e_ms, h2d, d2h = run_e2e(par, sc, fld, g0h, g1h, "f16", args.warmup, args.steps)
+
+    res = {}
+    for dt in ("f32", "f16"):
+        ms = forms[dt][0]
+        tot = allmax(ws, sum(ms) / 1e3)
+        res[dt] = {"mpix_s": ws * hw * len(ms) / tot / 1e6, "ms_per_step": 1e3 * tot / len(ms),
+                   "gbs": BYTES_PER_PIXEL[dt] * hw * len(ms) / tot / 1e9 / ws}
+    e2e_tot = allmax(ws, sum(e2e_ms) / 1e3)
+    e2e_v = ws * hw * len(e2e_ms) / e2e_tot / 1e6
+    if rank != 0:
+        return
+    peak, peak_kind = measured_hbm()
+    main = res["f16"]
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        px, sec, steps = oracle_strip_frames(16, args.cpu_budget)
+        cpu = {"value": px / sec / 1e6, "unit": "Mpix/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": "%d frames of a 1920x16 strip of the workload (frames 1..%d)" % (steps, steps)}
+    line = {
+        "metric": METRIC, "value": main["mpix_s"], "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "gamma_storage": "f16", "spp": 1, "width": 1920, "height": 1080,
+                   "l2": "flushed (256 MB write) before every timed frame",
+                   "parallelism": "dp%d (independent 1080p streams per GPU)" % ws},
+        "fp32_plain": {"value": res["f32"]["mpix_s"], "ms_per_step": res["f32"]["ms_per_step"],
+                       "roofline_frac": res["f32"]["gbs"] / peak},
+        "mse": mse,
+        "roofline": {"bound": "hbm", "achieved": main["gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": main["gbs"] / peak, "peak_kind": peak_kind,
+                     "kernel": "k_frame<f16> (fused guide pass)",
+                     "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL["f16"], "traffic": kernel_traffic(),
+                     "traffic_unit": "bytes per launch (ncu dram read+write, profiles/k_frame_1080p_pan.md)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_v, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "GuidePass.pg_frame with pinned-host G-buffer copies and image read-back"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=55)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=("native", "reference"))
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_gpu(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

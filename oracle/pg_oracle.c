@@ -595,8 +595,10 @@ void or_reproject(const or_config *cfg, const float *g0, const float *g1, const 
 /*   p_mix(w) = pi N(u)/(2 pi) + (1 - pi Z) p_b(w),  u = M^-1(w_local),     */
 /* and the one-sample balance-heuristic MIS estimate is F = f / p_mix.      */
 /* Random numbers: Philox4x32-10, key = seed, counter = (pixel, frame,      */
-/* sample, stream); stream 0 drives the strategy choice and Box-Muller,     */
-/* stream 1 the BRDF draw.                                                   */
+/* sample, stream). Word 0 of stream 0 picks the strategy; words 1 and 2    */
+/* drive either Box-Muller (guide) or the BRDF draw (they are independent   */
+/* of word 0, so still uniform given the choice); a guide draw that left    */
+/* the square takes its BRDF draw from words 0 and 1 of stream 1.           */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double g5[5], chol[3], Z, pi_eff;
@@ -698,9 +700,8 @@ static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_fi
             }
         } else {
             strat = S_BRDF;
-            or_philox(c1, key, r1);
             double mb;
-            valid = or_brdf_sample(p.rough, p.wo_l, unif(r1[0]), unif(r1[1]), wl, &mb);
+            valid = or_brdf_sample(p.rough, p.wo_l, unif(r0[1]), unif(r0[2]), wl, &mb);
             if (mb < margin) margin = mb;
         }
         double fcos = 0, pg = 0, pb = 0, pmix = 0, rad, uo[2] = {-1.0, -1.0};

@@ -235,7 +235,9 @@ pg_status pg_create(const pg_config* cfg, void* stream, pg_ctx** out) {
     P.init_c[0] = cfg->init_sigma[0];
     P.init_c[1] = cfg->init_sigma[1];
     P.init_c[2] = cfg->init_sigma[2];
-    gauss_legendre(pgk::kGL, P.gl_x, P.gl_w);
+    gauss_legendre(4, P.gl_x, P.gl_w);
+    gauss_legendre(6, P.gl_x + 4, P.gl_w + 4);
+    gauss_legendre(8, P.gl_x + 10, P.gl_w + 10);
 
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&c->gam[b], c->gam_bytes);

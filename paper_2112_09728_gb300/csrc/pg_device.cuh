@@ -15,7 +15,9 @@ constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kInv2Pi = 0.159154943091895335769f;
 constexpr float kInv4Pi2 = 0.0253302959105844428f;   // 1 / (4 pi^2)
 constexpr float k4OverPi = 1.27323954473516268615f;
-constexpr int kGL = 8;                               // Gauss-Legendre nodes for Phi_2
+// Gauss-Legendre tiers for the Phi_2 correction: 4 nodes for |rho| <= 0.6,
+// 6 for |rho| <= 0.75, 8 above (each keeps a corner's error near 1e-8 or below)
+constexpr int kGLTotal = 4 + 6 + 8;
 
 enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 enum { ST_BRDF = 0, ST_GUIDE = 1, ST_FALLBACK = 2, ST_INVALID = 4 };
@@ -37,8 +39,9 @@ struct Params {
     int n_lobes, mask_kind;
     float lobe_dir[8][3], lobe_kappa[8], lobe_scale[8];  // scale = amp * vMF normaliser
     float field_const, mask[3];
-    // Gauss-Legendre rule on [-1, 1] (computed on the host at context creation)
-    float gl_x[kGL], gl_w[kGL];
+    // Gauss-Legendre rules on [-1, 1] with 4, 6 and 8 nodes, back to back
+    // (computed on the host at context creation)
+    float gl_x[kGLTotal], gl_w[kGLTotal];
 };
 
 // ---------------------------------------------------------------------------
@@ -62,6 +65,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 __device__ __forceinline__ float unit24(uint32_t w) { return (float)(w >> 8) * 5.9604644775390625e-8f; }
 __device__ __forceinline__ float unit24_open0(uint32_t w) {
     return (float)((w >> 8) + 1u) * 5.9604644775390625e-8f;
+}
+
+// x / y for y > 0: the hardware reciprocal (2 ulp) while y is a normal number
+// far from the overflow of 1/y, a correctly rounded division otherwise (the
+// latter's slow path is then taken only for extreme operands).
+__device__ __forceinline__ float fdiv(float x, float y) { return y > 1e-30f ? __fdividef(x, y) : __fdiv_rn(x, y); }
+
+// sin and cos of 2 pi x for x in [0, 1): shifted by half a turn into [-pi, pi),
+// where the hardware approximation holds its 2^-21.4 absolute accuracy.
+__device__ __forceinline__ void sincos_turn(float x, float* s, float* c) {
+    float sn, cs;
+    __sincosf(6.28318530717958648f * (x - 0.5f), &sn, &cs);
+    *s = -sn;
+    *c = -cs;
 }
 
 // ---------------------------------------------------------------------------
@@ -106,13 +123,13 @@ __device__ __forceinline__ float3 square_to_hemi(float u, float v) {
     if (fabsf(a) > fabsf(b)) {
         r = a;
         m = fminf(u, 1.0f - u);
-        sincospif(0.25f * (b / a), &s, &c);
+        __sincosf(0.78539816339744831f * __fdividef(b, a), &s, &c);
         dx = r * c;
         dy = r * s;
     } else {
         r = b;
         m = fminf(v, 1.0f - v);
-        sincospif(0.25f * (a / b), &s, &c);
+        __sincosf(0.78539816339744831f * __fdividef(a, b), &s, &c);
         dx = r * s;
         dy = r * c;
     }
@@ -129,14 +146,14 @@ __device__ __forceinline__ float2 hemi_to_square(float3 w) {
     const float inv = rsqrtf(1.0f + z);
     const float dx = w.x * inv, dy = w.y * inv;
     const float r = sqrtf(dx * dx + dy * dy);
-    if (r == 0.0f) return make_float2(0.5f, 0.5f);
+    if (r < 1e-30f) return make_float2(0.5f, 0.5f);   // the pole (to within 1e-30)
     float a, b;
     if (fabsf(dx) >= fabsf(dy)) {
         a = copysignf(r, dx);
-        b = a * k4OverPi * atanf(dy / dx);
+        b = a * k4OverPi * atanf(__fdividef(dy, dx));
     } else {
         b = copysignf(r, dy);
-        a = b * k4OverPi * atanf(dx / dy);
+        a = b * k4OverPi * atanf(__fdividef(dx, dy));
     }
     return make_float2(0.5f * (a + 1.0f), 0.5f * (b + 1.0f));
 }
@@ -328,40 +345,58 @@ struct Guide {
     float Z, pi_eff;
 };
 
-// Phi_2 correction of the four corners by the Drezner-Wesolowsky form:
-// Phi_2(h,k;rho) = Phi(h)Phi(k) + 1/(2 pi) int_0^asin(rho) exp(-(h^2+k^2-2hk sin t)/(2 cos^2 t)) dt,
-// the t-integral by an 8-node Gauss-Legendre rule (abs. error ~1e-8 for |rho| <= 0.9).
-// Corners with h^2 + k^2 > 100 are skipped: their integrand is below e^-25.
-__device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, float sx, float sy, float rho) {
-    const float h0 = -mx / sx, h1 = (1.0f - mx) / sx;
-    const float k0 = -my / sy, k1 = (1.0f - my) / sy;
-    const float rs2 = 0.70710678118654752f;
-    const float dpx = 1.0f - 0.5f * erfcf(-h0 * rs2) - 0.5f * erfcf(h1 * rs2);
-    const float dpy = 1.0f - 0.5f * erfcf(-k0 * rs2) - 0.5f * erfcf(k1 * rs2);
+// sin t for |t| <= 1.2 by its Taylor series through t^13 (remainder below
+// 1.2e-11): the nodes of the Phi_2 rule never leave [-asin 0.9, asin 0.9].
+__device__ __forceinline__ float sin_small(float t) {
+    const float t2 = t * t;
+    float p = 1.6059043836821613e-10f;           //  1/13!
+    p = fmaf(p, t2, -2.5052108385441720e-8f);    // -1/11!
+    p = fmaf(p, t2, 2.7557319223985891e-6f);     //  1/9!
+    p = fmaf(p, t2, -1.9841269841269841e-4f);    // -1/7!
+    p = fmaf(p, t2, 8.3333333333333333e-3f);     //  1/5!
+    p = fmaf(p, t2, -1.6666666666666667e-1f);    // -1/3!
+    return fmaf(t * t2, p, t);
+}
+
+// Upper tail 1 - Phi(h) = erfc(h / sqrt 2) / 2 for h >= 0; below 8e-9 past
+// h = 5.66, where it is dropped.
+__device__ __forceinline__ float normal_tail(float h) {
+    return h < 5.66f ? 0.5f * erfcf(h * 0.70710678118654752f) : 0.0f;
+}
+
+// Z by four corners of the bivariate normal cdf in the Drezner-Wesolowsky form
+//   Phi_2(h,k;rho) = Phi(h)Phi(k) + 1/(2 pi) int_0^asin(rho) exp(-(h^2+k^2-2hk sin t)/(2 cos^2 t)) dt,
+// so Z = (Phi(h1)-Phi(h0)) (Phi(k1)-Phi(k0)) + signed sum of the four corner
+// integrals, each by a Gauss-Legendre rule in t of 4, 6 or 8 nodes chosen by
+// |rho| (abs. error ~1e-8 up to |rho| = 0.9). As (h^2+k^2-2hks)/cos^2 t >=
+// max(h^2, k^2), a corner with max(h^2, k^2) > 50 contributes below e^-25
+// and is skipped.
+__device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, float isx, float isy, float rho) {
+    const float h0 = -mx * isx, h1 = (1.0f - mx) * isx;
+    const float k0 = -my * isy, k1 = (1.0f - my) * isy;
+    const float dpx = 1.0f - normal_tail(-h0) - normal_tail(h1);
+    const float dpy = 1.0f - normal_tail(-k0) - normal_tail(k1);
     float z = dpx * dpy;
-    if (rho != 0.0f) {
-        const float asr = asinf(rho);
-        float st[kGL], ic[kGL];
-#pragma unroll
-        for (int i = 0; i < kGL; ++i) {
-            float s, c;
-            sincosf(0.5f * asr * (1.0f + P.gl_x[i]), &s, &c);
-            st[i] = s;
-            ic[i] = 0.5f / (c * c);
-        }
+    const float h0s = h0 * h0, h1s = h1 * h1, k0s = k0 * k0, k1s = k1 * k1;
+    const bool c00 = fmaxf(h0s, k0s) <= 50.0f, c10 = fmaxf(h1s, k0s) <= 50.0f;
+    const bool c01 = fmaxf(h0s, k1s) <= 50.0f, c11 = fmaxf(h1s, k1s) <= 50.0f;
+    if (rho != 0.0f && (c00 || c10 || c01 || c11)) {
+        const float ar = fabsf(rho);
+        const int first = ar <= 0.6f ? 0 : (ar <= 0.75f ? 4 : 10);
+        const int last = ar <= 0.6f ? 4 : (ar <= 0.75f ? 10 : kGLTotal);
+        const float asr = asinf(rho), half = 0.5f * asr;
         float acc = 0.0f;
-#pragma unroll
-        for (int cn = 0; cn < 4; ++cn) {
-            const float h = (cn & 1) ? h1 : h0, k = (cn & 2) ? k1 : k0;
-            const float sign = ((cn == 0) || (cn == 3)) ? 1.0f : -1.0f;
-            const float hk2 = h * h + k * k, hk = 2.0f * h * k;
-            if (hk2 > 100.0f) continue;
-            float s = 0.0f;
-#pragma unroll
-            for (int i = 0; i < kGL; ++i) s += P.gl_w[i] * expf(-(hk2 - hk * st[i]) * ic[i]);
-            acc += sign * s;
+        for (int i = first; i < last; ++i) {
+            const float s = sin_small(fmaf(half, P.gl_x[i], half));
+            const float ic = __fdividef(-0.5f, fmaf(-s, s, 1.0f));      // -1 / (2 cos^2 t), cos^2 t >= 0.19
+            float v = 0.0f;
+            if (c00) v += __expf((h0s + k0s - 2.0f * h0 * k0 * s) * ic);
+            if (c11) v += __expf((h1s + k1s - 2.0f * h1 * k1 * s) * ic);
+            if (c10) v -= __expf((h1s + k0s - 2.0f * h1 * k0 * s) * ic);
+            if (c01) v -= __expf((h0s + k1s - 2.0f * h0 * k1 * s) * ic);
+            acc = fmaf(P.gl_w[i], v, acc);
         }
-        z += acc * (0.5f * asr) * kInv2Pi;
+        z = fmaf(acc, half * kInv2Pi, z);
     }
     return z;
 }
@@ -372,17 +407,18 @@ __device__ __forceinline__ Guide derive_guide(const Params& P, const Gam& g, boo
     d.my = fminf(fmaxf(g.ey, 0.0f), 1.0f);
     d.sxx = fmaxf(g.sxx, P.sigma2_min);
     d.syy = fmaxf(g.syy, P.sigma2_min);
-    const float lim = P.rho_max * sqrtf(d.sxx * d.syy);
+    const float isy = rsqrtf(d.syy);
+    d.il11 = rsqrtf(d.sxx);
+    const float lim = P.rho_max * d.sxx * d.il11 * d.syy * isy;   // rho_max sqrt(sxx syy)
     d.sxy = fminf(fmaxf(g.sxy, -lim), lim);
-    d.l11 = sqrtf(d.sxx);
-    d.l21 = d.sxy / d.l11;
-    d.l22 = sqrtf(fmaf(-d.l21, d.l21, d.syy));
-    d.il11 = 1.0f / d.l11;
-    d.il22 = 1.0f / d.l22;
+    d.l11 = d.sxx * d.il11;
+    d.l21 = d.sxy * d.il11;
+    const float c22 = fmaf(-d.l21, d.l21, d.syy);
+    d.il22 = rsqrtf(c22);
+    d.l22 = c22 * d.il22;
     d.pnorm = kInv4Pi2 * d.il11 * d.il22;
     d.pi_eff = gated ? 0.0f : g.pi;
-    d.Z = (d.pi_eff > 0.0f) ? rect_mass(P, d.mx, d.my, d.l11, sqrtf(d.syy), d.sxy / (d.l11 * sqrtf(d.syy)))
-                            : 1.0f;
+    d.Z = (d.pi_eff > 0.0f) ? rect_mass(P, d.mx, d.my, d.il11, isy, d.sxy * d.il11 * isy) : 1.0f;
     return d;
 }
 
@@ -390,7 +426,7 @@ __device__ __forceinline__ Guide derive_guide(const Params& P, const Gam& g, boo
 __device__ __forceinline__ float guide_pdf(const Guide& d, float ux, float uy) {
     const float y1 = (ux - d.mx) * d.il11;
     const float y2 = (uy - d.my - d.l21 * y1) * d.il22;
-    return expf(-0.5f * (y1 * y1 + y2 * y2)) * d.pnorm;
+    return __expf(-0.5f * (y1 * y1 + y2 * y2)) * d.pnorm;
 }
 
 // ---------------------------------------------------------------------------
@@ -405,8 +441,13 @@ struct Surf {
     float3 pos;     // world shading point
     float a2;       // alpha^2 (GGX)
     float albedo;
+    float go;       // GGX: albedo G1(w_o) / (4 cos theta_o), 0 when back-facing
     bool lambert;
 };
+
+__device__ __forceinline__ float smith_g1(float a2, float c) {
+    return __fdividef(2.0f * c, c + sqrtf(fmaf(1.0f - a2, c * c, a2)));
+}
 
 __device__ __forceinline__ Surf make_surf(const Params& P, int x, int y, float4 g0, float4 g1) {
     Surf s;
@@ -432,11 +473,8 @@ __device__ __forceinline__ Surf make_surf(const Params& P, int x, int y, float4 
     const float a = fmaxf(g1.z * g1.z, 1e-4f);
     s.a2 = a * a;
     s.albedo = g1.w;
+    s.go = s.wo.z > 0.0f ? fdiv(g1.w * smith_g1(s.a2, s.wo.z), 4.0f * s.wo.z) : 0.0f;
     return s;
-}
-
-__device__ __forceinline__ float smith_g1(float a2, float c) {
-    return 2.0f * c / (c + sqrtf(fmaf(1.0f - a2, c * c, a2)));
 }
 
 // f_r cos(theta_i) and the BRDF draw's density (per steradian) at local wi.
@@ -458,25 +496,26 @@ __device__ __forceinline__ void brdf_eval(const Surf& s, float3 wi, float& fcos,
     }
     const float3 h = make_float3(s.wo.x + wi.x, s.wo.y + wi.y, s.wo.z + wi.z);
     const float hz2 = h.z * h.z, hxy2 = h.x * h.x + h.y * h.y, hl2 = hz2 + hxy2;
-    const float t = (s.a2 * hz2 + hxy2) / hl2;           // (n.h)^2 (a^2 - 1) + 1, cancellation-free
-    const float D = s.a2 / (kPi * t * t);
+    // (n.h)^2 (a^2 - 1) + 1 = (a^2 h_z^2 + h_x^2 + h_y^2) / |h|^2, free of cancellation
+    const float t = fdiv(fmaf(s.a2, hz2, hxy2), hl2);   // in [a^2, 1]
+    const float D = __fdividef(s.a2, kPi * t * t);
     const float ihl = rsqrtf(hl2);
     const float nh = h.z * ihl, oh = dot3(s.wo, h) * ihl;
-    fcos = s.albedo * D * smith_g1(s.a2, wi.z) * smith_g1(s.a2, s.wo.z) / (4.0f * s.wo.z);
-    pb = oh > 0.0f ? D * nh / (4.0f * oh) : 0.0f;
+    fcos = D * smith_g1(s.a2, wi.z) * s.go;
+    pb = oh > 0.0f ? fdiv(D * nh, 4.0f * oh) : 0.0f;
 }
 
 // BRDF draw from two uniforms; false for a wasted draw (below the horizon).
 __device__ __forceinline__ bool brdf_sample(const Surf& s, float x1, float x2, float3& wi) {
     float sn, cs;
-    sincospif(2.0f * x2, &sn, &cs);
+    sincos_turn(x2, &sn, &cs);
     if (s.lambert) {
         const float r = sqrtf(x1);
         wi = make_float3(r * cs, r * sn, sqrtf(1.0f - x1));
         return true;
     }
-    const float den = (1.0f - x1) + s.a2 * x1;
-    const float ct = sqrtf((1.0f - x1) / den), st = sqrtf(s.a2 * x1 / den);
+    const float id = __fdividef(1.0f, (1.0f - x1) + s.a2 * x1);
+    const float ct = sqrtf((1.0f - x1) * id), st = sqrtf(s.a2 * x1 * id);
     const float3 h = make_float3(st * cs, st * sn, ct);
     const float oh = dot3(s.wo, h);
     wi = make_float3(2.0f * oh * h.x - s.wo.x, 2.0f * oh * h.y - s.wo.y, 2.0f * oh * h.z - s.wo.z);
@@ -492,7 +531,7 @@ __device__ __forceinline__ float radiance(const Params& P, float3 pos, float3 w)
     float s = 0.0f;
     for (int j = 0; j < P.n_lobes; ++j) {
         const float dx = w.x - P.lobe_dir[j][0], dy = w.y - P.lobe_dir[j][1], dz = w.z - P.lobe_dir[j][2];
-        s += P.lobe_scale[j] * expf(-0.5f * P.lobe_kappa[j] * (dx * dx + dy * dy + dz * dz));
+        s = fmaf(P.lobe_scale[j], __expf(-0.5f * P.lobe_kappa[j] * (dx * dx + dy * dy + dz * dz)), s);
     }
     if (P.mask_kind == 1) {
         const float m = 0.5f + 0.5f * sinpif(2.0f * (P.mask[0] * pos.x + P.mask[2] * w.x)) *
@@ -535,14 +574,18 @@ __device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, con
     const float wg = d.pi_eff * o.pg;
     o.pmix = wg + wb;
     if (o.pmix > 0.0f) {
-        o.F = o.fcos / o.pmix;
-        o.mis = ((o.strat & 3) == ST_GUIDE ? wg : wb) / o.pmix;
+        o.F = fdiv(o.fcos, o.pmix);
+        o.mis = fdiv((o.strat & 3) == ST_GUIDE ? wg : wb, o.pmix);
     } else {
         o.F = 0.0f;
         o.mis = 0.0f;
     }
 }
 
+// Random numbers: word 0 of Philox stream 0 picks the strategy; words 1 and 2
+// drive Box-Muller for a guide draw or the BRDF draw otherwise (independent of
+// word 0, hence still uniform given the choice); a guide draw that left the
+// square takes its BRDF draw from stream 1.
 __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, const Surf& s, uint32_t pix,
                                            uint32_t frame, uint32_t si) {
     Smp o;
@@ -551,9 +594,9 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
     bool have_u = false, valid;
     if (zeta < d.pi_eff) {
         const float x1 = unit24_open0(r0.y), x2 = unit24(r0.z);
-        const float rr = sqrtf(-2.0f * logf(x1));
+        const float rr = sqrtf(-2.0f * __logf(x1));
         float sn, cs;
-        sincospif(2.0f * x2, &sn, &cs);
+        sincos_turn(x2, &sn, &cs);
         const float z1 = rr * cs, z2 = rr * sn;
         o.ux = fmaf(d.l11, z1, d.mx);
         o.uy = fmaf(d.l22, z2, fmaf(d.l21, z1, d.my));
@@ -564,13 +607,12 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
             have_u = true;
         } else {
             o.strat = ST_FALLBACK;
+            const uint4 r1 = philox4x32_10(make_uint4(pix, frame, si, 1u), P.key0, P.key1);
+            valid = brdf_sample(s, unit24(r1.x), unit24(r1.y), o.wl);
         }
     } else {
         o.strat = ST_BRDF;
-    }
-    if (!have_u) {
-        const uint4 r1 = philox4x32_10(make_uint4(pix, frame, si, 1u), P.key0, P.key1);
-        valid = brdf_sample(s, unit24(r1.x), unit24(r1.y), o.wl);
+        valid = brdf_sample(s, unit24(r0.y), unit24(r0.z), o.wl);
     }
     if (!valid) o.strat |= ST_INVALID;
     eval_sample(P, d, s, o, have_u);
@@ -619,7 +661,7 @@ struct Stats {
 //   E <- ((1-eta) pi M0 E + eta S) / A,  pi <- clamp(A/B),  W <- B,  k <- k+1.
 // The moment update is applied about the stored mean: with lambda = eta a / A,
 // delta = S1/a and M2 = S2/a (batch offset and second moment about E[X]),
-//   mu' = mu + lambda delta,  Sigma' = (1-lambda) Sigma + lambda M2 - lambda^2 delta delta^T,
+//   mu' = mu + lambda delta,  Sigma' = (1-lambda) Sigma + lambda M2 - (lambda delta)(lambda delta)^T,
 // the same update in exact arithmetic, free of the cancellation of raw second
 // moments in binary32. A frame with b = 0 changes nothing.
 __device__ __forceinline__ void m_step(const Params& P, Gam& g, const Stats& st) {
@@ -634,17 +676,20 @@ __device__ __forceinline__ void m_step(const Params& P, Gam& g, const Stats& st)
     const float A = fmaf(eta, a, keep);
     const float B = fmaf(eta, b, e1 * m0);
     if (a > 0.0f && A > 0.0f) {
-        const float lam = __fdiv_rn(eta * a, A), l1 = 1.0f - lam, l2 = lam * lam;
-        const float dx = __fdiv_rn(st.s1x.s, a), dy = __fdiv_rn(st.s1y.s, a);
-        const float mxx = __fdiv_rn(st.s2xx.s, a), myy = __fdiv_rn(st.s2yy.s, a), mxy = __fdiv_rn(st.s2xy.s, a);
-        g.sxx = fmaf(l1, g.sxx, fmaf(lam, mxx, -l2 * dx * dx));
-        g.syy = fmaf(l1, g.syy, fmaf(lam, myy, -l2 * dy * dy));
-        g.sxy = fmaf(l1, g.sxy, fmaf(lam, mxy, -l2 * dx * dy));
-        g.ex = fmaf(lam, dx, g.ex);
-        g.ey = fmaf(lam, dy, g.ey);
+        // lambda delta = eta S1 / A and lambda M2 = eta S2 / A: bounded ratios,
+        // formed without a reciprocal of a or A (either may be subnormal)
+        const float lam = fdiv(eta * a, A), l1 = 1.0f - lam;
+        const float ldx = fdiv(eta * st.s1x.s, A), ldy = fdiv(eta * st.s1y.s, A);
+        const float lmxx = fdiv(eta * st.s2xx.s, A), lmyy = fdiv(eta * st.s2yy.s, A);
+        const float lmxy = fdiv(eta * st.s2xy.s, A);
+        g.sxx = fmaf(l1, g.sxx, fmaf(-ldx, ldx, lmxx));
+        g.syy = fmaf(l1, g.syy, fmaf(-ldy, ldy, lmyy));
+        g.sxy = fmaf(l1, g.sxy, fmaf(-ldx, ldy, lmxy));
+        g.ex += ldx;
+        g.ey += ldy;
         raw_from_central(g);
     }
-    g.pi = fminf(fmaxf(__fdiv_rn(A, B), P.pi_min), P.pi_max);
+    g.pi = fminf(fmaxf(fdiv(A, B), P.pi_min), P.pi_max);
     g.W = B;
     g.k = fminf(k + 1.0f, (float)P.k_max);
 }

@@ -56,7 +56,7 @@ __device__ __forceinline__ bool reproject_pixel(const Params& P, int x, int y, f
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kBlock) k_frame(const Params P, const void* __restrict__ gin,
+__global__ void __launch_bounds__(kBlock, 4) k_frame(const Params P, const void* __restrict__ gin,
                                                   void* __restrict__ gout, const float4* __restrict__ g0,
                                                   const float4* __restrict__ g1, const float4* __restrict__ g0p,
                                                   float* __restrict__ img, uint32_t frame, int* __restrict__ err) {
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kBlock) k_frame(const Params P, const void* __
     m_step(P, g, st);
     if (!gam_finite(g)) atomicOr(err, 1);
     Store<DT>::store(gout, hw, (size_t)i, g);
-    if (img) __stcs(img + i, __fdiv_rn(f.s, (float)P.spp));
+    if (img) __stcs(img + i, fdiv(f.s, (float)P.spp));
 }
 
 template <int DT>
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kBlock) k_sample(const Params P, const float4*
         if (out.estimate) out.estimate[q] = o.F;
         if (out.strategy) out.strategy[q] = (uint8_t)o.strat;
     }
-    if (img) img[i] = __fdiv_rn(f.s, (float)P.spp);
+    if (img) img[i] = fdiv(f.s, (float)P.spp);
 }
 
 // Training pass on given samples (Sec. 3.2): the E-step re-evaluates each
