@@ -1,0 +1,154 @@
+// Host-side construction and validation of the launch parameters.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "pg_params.h"
+
+namespace pgk {
+
+namespace {
+
+// Gauss-Legendre rule on [-1, 1]: nodes are the roots of P_n found by Newton
+// iteration from Chebyshev-like starting points, weights 2/((1-x^2) P_n'(x)^2).
+void gauss_legendre(int n, float* x_out, float* w_out) {
+    for (int i = 0; i < n; ++i) {
+        double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (x * p1 - p0) / (x * x - 1.0);
+        x_out[i] = (float)x;
+        w_out[i] = (float)(2.0 / ((1.0 - x * x) * dp * dp));
+    }
+}
+
+}  // namespace
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+pg_status check_config(const pg_config* c, std::string& why) {
+    char buf[160];
+    if (c->width < 1 || c->width > 32768 || c->height < 1 || c->height > 32768) {
+        std::snprintf(buf, sizeof buf, "width/height %d x %d outside [1, 32768]", c->width, c->height);
+        why = buf;
+        return PG_ERR_ARG;
+    }
+    if ((int64_t)c->width * c->height > (int64_t)1 << 30) { why = "more than 2^30 pixels"; return PG_ERR_ARG; }
+    if (c->spp < 1 || c->spp > 1024) { why = "spp outside [1, 1024]"; return PG_ERR_ARG; }
+    if (c->gamma_dtype < PG_F32 || c->gamma_dtype > PG_BF16) { why = "unknown gamma_dtype"; return PG_ERR_ARG; }
+    if (c->k_max < 0 || c->k_max > 1 << 20) { why = "k_max outside [0, 2^20]"; return PG_ERR_ARG; }
+    if (!(c->pi_min >= 0.0f && c->pi_min <= c->pi_max && c->pi_max <= 1.0f)) {
+        why = "need 0 <= pi_min <= pi_max <= 1";
+        return PG_ERR_ARG;
+    }
+    if (!(c->pi_reinit >= 0.0f && c->pi_reinit <= 1.0f) || !(c->init_pi >= 0.0f && c->init_pi <= 1.0f)) {
+        why = "pi_reinit / init_pi outside [0, 1]";
+        return PG_ERR_ARG;
+    }
+    if (!(c->sigma2_min > 0.0f) || !(c->rho_max >= 0.0f && c->rho_max < 1.0f)) {
+        why = "need sigma2_min > 0 and 0 <= rho_max < 1";
+        return PG_ERR_ARG;
+    }
+    if (!(c->depth_tol >= 0.0f) || !std::isfinite(c->normal_tol) || !std::isfinite(c->rough_min)) {
+        why = "bad depth_tol / normal_tol / rough_min";
+        return PG_ERR_ARG;
+    }
+    if (!(c->init_sigma[0] > 0.0f && c->init_sigma[1] > 0.0f) ||
+        !(c->init_sigma[2] * c->init_sigma[2] < c->init_sigma[0] * c->init_sigma[1]) ||
+        !(c->init_mu[0] >= 0.0f && c->init_mu[0] <= 1.0f && c->init_mu[1] >= 0.0f && c->init_mu[1] <= 1.0f)) {
+        why = "initial guide must have mu in [0,1]^2 and a positive definite covariance";
+        return PG_ERR_ARG;
+    }
+    return PG_OK;
+}
+
+void config_params(const pg_config& cfg, Params& P) {
+    std::memset(&P, 0, sizeof P);
+    P.W = cfg.width;
+    P.H = cfg.height;
+    P.spp = cfg.spp;
+    P.k_max = cfg.k_max;
+    P.key0 = (uint32_t)(cfg.seed & 0xffffffffu);
+    P.key1 = (uint32_t)(cfg.seed >> 32);
+    P.pi_min = cfg.pi_min;
+    P.pi_max = cfg.pi_max;
+    P.pi_reinit = cfg.pi_reinit;
+    P.depth_tol = cfg.depth_tol;
+    P.normal_tol = cfg.normal_tol;
+    P.rough_min = cfg.rough_min;
+    P.sigma2_min = cfg.sigma2_min;
+    P.rho_max = cfg.rho_max;
+    const double mx = cfg.init_mu[0], my = cfg.init_mu[1];
+    P.init_raw[0] = (float)mx;
+    P.init_raw[1] = (float)my;
+    P.init_raw[2] = (float)(cfg.init_sigma[0] + mx * mx);
+    P.init_raw[3] = (float)(cfg.init_sigma[1] + my * my);
+    P.init_raw[4] = (float)(cfg.init_sigma[2] + mx * my);
+    P.init_c[0] = cfg.init_sigma[0];
+    P.init_c[1] = cfg.init_sigma[1];
+    P.init_c[2] = cfg.init_sigma[2];
+    gauss_legendre(4, P.gl_x, P.gl_w);
+    gauss_legendre(6, P.gl_x + 4, P.gl_w + 4);
+    gauss_legendre(8, P.gl_x + 10, P.gl_w + 10);
+}
+
+pg_status camera_params(const pg_camera& cam, Params& P, std::string& why) {
+    if (cam.kind != 0 && cam.kind != 1) {
+        why = "camera kind must be 0 or 1";
+        return PG_ERR_ARG;
+    }
+    P.cam_kind = cam.kind;
+    for (int k = 0; k < 3; ++k) {
+        P.cam_o[k] = cam.origin[k];
+        P.cam_f[k] = cam.fwd[k];
+        P.cam_r[k] = cam.right[k];
+        P.cam_u[k] = cam.up[k];
+    }
+    P.cam_ps = cam.pixel_size;
+    P.cam_tan = cam.tan_half_fov;
+    P.cam_aspect = (float)P.W / (float)P.H;
+    return PG_OK;
+}
+
+pg_status field_params(const pg_field* f, Params& P, std::string& why) {
+    if (!f) { why = "field is NULL"; return PG_ERR_ARG; }
+    if (f->n_lobes < 0 || f->n_lobes > 8) { why = "n_lobes outside [0, 8]"; return PG_ERR_ARG; }
+    if (f->mask_kind != 0 && f->mask_kind != 1) { why = "mask_kind must be 0 or 1"; return PG_ERR_ARG; }
+    P.n_lobes = f->n_lobes;
+    for (int j = 0; j < 8; ++j) {
+        for (int k = 0; k < 3; ++k) P.lobe_dir[j][k] = j < f->n_lobes ? f->dir[j][k] : 0.0f;
+        if (j < f->n_lobes) {
+            const double kap = f->kappa[j];
+            if (!(kap > 0.0) || !std::isfinite(kap)) { why = "lobe kappa must be > 0"; return PG_ERR_ARG; }
+            // normalised vMF on the sphere: kappa / (2 pi (1 - exp(-2 kappa)))
+            P.lobe_kappa[j] = (float)kap;
+            P.lobe_scale[j] = (float)((double)f->amp[j] * kap / (2.0 * M_PI * -std::expm1(-2.0 * kap)));
+        } else {
+            P.lobe_kappa[j] = 0.0f;
+            P.lobe_scale[j] = 0.0f;
+        }
+    }
+    P.field_const = f->constant;
+    P.mask_kind = f->mask_kind;
+    for (int k = 0; k < 3; ++k) P.mask[k] = f->mask[k];
+    return PG_OK;
+}
+
+}  // namespace pgk
