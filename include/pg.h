@@ -192,6 +192,31 @@ pg_status pg_frame(pg_ctx *ctx, const pg_gbuffer *cur, const float *d_g0_prev,
 pg_status pg_eval(pg_ctx *ctx, const pg_gbuffer *cur, const pg_field *field, int32_t n_dirs,
                   const float *d_dirs, float *d_out);
 
+/* A whole staged frame (pg_reproject + pg_sample + pg_update) without a
+ * context and without allocating any device memory, for callers that cannot
+ * call cudaMalloc (an engine whose device memory is handed out by its own
+ * allocator, code that must not allocate while frames are in flight). The
+ * paper has no counterpart: it is a deployment variant of the staged pass.
+ *   cfg          validated as in pg_create; width*height must not exceed
+ *                262144 pixels (PG_ERR_ARG and a message on stderr otherwise)
+ *   d_gamma_in   Gamma(t-1) in cfg->gamma_dtype's storage layout (read)
+ *   d_gamma_out  Gamma(t), same layout (written); may equal d_gamma_in but
+ *                must not otherwise overlap it
+ *   d_samples    per-sample records as for pg_sample; wx, wy, wz, radiance
+ *                and strategy are required, the other planes may be NULL
+ *   d_img        per-pixel mean estimate (nullable); stream: a cudaStream_t
+ * The work copy of Gamma lives in a fixed 8 MiB device array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits. The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture. All
+ * calls share the array and overwrite it, so calls whose work overlaps on the
+ * GPU (different streams, different threads) race: order them on one stream.
+ * A non-finite Gamma is not reported (there is no context to hold the flag). */
+pg_status pg_frame_noalloc(const pg_config *cfg, const pg_gbuffer *cur, const float *d_g0_prev,
+                           const pg_field *field, uint32_t frame, const void *d_gamma_in,
+                           void *d_gamma_out, const pg_samples *d_samples, float *d_img,
+                           void *stream);
+
 /* Raw Gamma in its storage layout (pg_gamma_bytes bytes): checkpoint and
  * resume. Copies are stream-ordered; with a host buffer the call waits. */
 size_t pg_gamma_bytes(const pg_ctx *ctx);

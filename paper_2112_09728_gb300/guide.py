@@ -67,23 +67,29 @@ def alloc_samples(spp, hw, device="cuda"):
     return d
 
 
+def make_config(width, height, spp=1, gamma_dtype="f32", seed=0, **overrides) -> L.pg_config:
+    """pg_config with the library's defaults and the given overrides."""
+    cfg = L.pg_config()
+    L.load().pg_config_default(C.byref(cfg), int(width), int(height))
+    cfg.spp = int(spp)
+    cfg.gamma_dtype = _DTYPES[gamma_dtype]
+    cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    for k, v in overrides.items():
+        if k in ("init_mu", "init_sigma"):
+            getattr(cfg, k)[:] = [float(x) for x in v]
+        elif k == "k_max":
+            cfg.k_max = int(v)
+        else:
+            setattr(cfg, k, float(v))
+    return cfg
+
+
 class GuidePass:
     """One guide-pass context (pg_ctx): owns Gamma on the current device."""
 
     def __init__(self, width, height, spp=1, gamma_dtype="f32", seed=0, **overrides):
         self._lib = L.load()
-        cfg = L.pg_config()
-        self._lib.pg_config_default(C.byref(cfg), int(width), int(height))
-        cfg.spp = int(spp)
-        cfg.gamma_dtype = _DTYPES[gamma_dtype]
-        cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
-        for k, v in overrides.items():
-            if k in ("init_mu", "init_sigma"):
-                getattr(cfg, k)[:] = [float(x) for x in v]
-            elif k == "k_max":
-                cfg.k_max = int(v)
-            else:
-                setattr(cfg, k, float(v))
+        cfg = make_config(width, height, spp, gamma_dtype, seed, **overrides)
         self.cfg = cfg
         self.width, self.height, self.spp = int(width), int(height), int(spp)
         self.hw = self.width * self.height
@@ -229,6 +235,33 @@ def pg_philox(ctr, key, use_curand=False):
     if st != L.PG_OK:
         raise L.PgError(st, "pg_philox")
     return out
+
+
+def pg_frame_noalloc(cfg, g0, g1, camera, g0_prev, field, frame, gamma_in, gamma_out, samples, img=None):
+    """One staged frame without a context and without device allocation (see
+    include/pg.h). gamma_in / gamma_out: uint8 CUDA tensors of the storage
+    layout's size; samples: dict of sample planes (alloc_samples)."""
+    lib = L.load()
+    hw = int(cfg.width) * int(cfg.height)
+    gb = L.pg_gbuffer()
+    gb.g0 = _ptr(g0, what="g0", align16=True)
+    gb.g1 = _ptr(g1, what="g1", align16=True)
+    gb.camera = make_camera(camera)
+    ps = L.pg_samples()
+    for k in SAMPLE_FLOAT_PLANES:
+        setattr(ps, k, _ptr(samples.get(k), what=k))
+    ps.strategy = _ptr(samples.get("strategy"), dtype=torch.uint8, what="strategy")
+    for t, n, what in ((g0, 4 * hw, "g0"), (g1, 4 * hw, "g1"), (g0_prev, 4 * hw, "g0_prev")):
+        if t.numel() != n:
+            raise ValueError("%s must have %d elements" % (what, n))
+    st = lib.pg_frame_noalloc(C.byref(cfg), C.byref(gb), C.c_void_p(_ptr(g0_prev, what="g0_prev", align16=True)),
+                              C.byref(make_field(field)), C.c_uint32(int(frame) & 0xFFFFFFFF),
+                              C.c_void_p(_ptr(gamma_in, dtype=torch.uint8, what="gamma_in", align16=True)),
+                              C.c_void_p(_ptr(gamma_out, dtype=torch.uint8, what="gamma_out", align16=True)),
+                              C.byref(ps), C.c_void_p(_ptr(img, what="img")),
+                              C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != L.PG_OK:
+        raise L.PgError(st, "pg_frame_noalloc")
 
 
 def planes_to_rows(planes):
