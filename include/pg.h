@@ -192,6 +192,35 @@ pg_status pg_frame(pg_ctx *ctx, const pg_gbuffer *cur, const float *d_g0_prev,
 pg_status pg_eval(pg_ctx *ctx, const pg_gbuffer *cur, const pg_field *field, int32_t n_dirs,
                   const float *d_dirs, float *d_out);
 
+/* The differentiable form of the guide (not in the paper; a per-pixel
+ * variance objective beside the EM step of Sec. 3.2). With theta =
+ * (mu_x, mu_y, s_xx, s_yy, s_xy, pi) the guide's regularised mean,
+ * covariance and mixing weight, n_samples directions w_i are drawn from the
+ * guide at theta (Philox streams 2 and 3 of `frame`) and the loss is the Monte
+ * Carlo second moment of the estimator, l = 1/n sum f_i^2 / p(w_i)^2; its
+ * gradient with the draws held fixed is
+ *   dl/dtheta = -1/n sum f_i^2 (dp/dtheta)(w_i) / p(w_i)^3,
+ * including the dependence of the mixture pdf on Z. s_xy is one parameter
+ * (its derivative covers both off-diagonal entries). A pixel whose guide is
+ * gated off has a loss and a zero gradient.
+ *   d_theta  [6][H*W] planes (nullable: theta of the current Gamma)
+ *   d_loss   [H*W];  d_grad [6][H*W] planes. */
+pg_status pg_grad(pg_ctx *ctx, const pg_gbuffer *cur, const pg_field *field, uint32_t frame,
+                  int32_t n_samples, const float *d_theta, float *d_loss, float *d_grad);
+
+/* One Adam step (Kingma & Ba) on theta of every pixel from d_grad
+ * ([6][H*W]), projected back onto the guide's domain (mean in [0,1]^2,
+ * variances >= sigma2_min, |rho| <= rho_max, pi in [pi_min, pi_max]) and
+ * written into Gamma as moments; k and W are kept. The context owns the
+ * moments (allocated on first use); step = 1 restarts them from zero. */
+pg_status pg_adam_step(pg_ctx *ctx, const float *d_grad, float lr, float beta1, float beta2, float eps,
+                       int32_t step);
+
+/* theta of every pixel ([6][H*W] planes) from Gamma, and back (projected as
+ * in pg_adam_step; k and W are kept). */
+pg_status pg_theta_from_gamma(pg_ctx *ctx, float *d_theta);
+pg_status pg_theta_to_gamma(pg_ctx *ctx, const float *d_theta);
+
 /* A whole staged frame (pg_reproject + pg_sample + pg_update) without a
  * context and without allocating any device memory, for callers that cannot
  * call cudaMalloc (an engine whose device memory is handed out by its own

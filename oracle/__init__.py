@@ -94,6 +94,9 @@ def _load():
                 "or_frame": [_P, _P, _P, C.c_uint32, _P, _P, _P, _P, _P, _P, _P, _P],
                 "or_eval": [_P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P],
                 "or_derive_pixels": [_P, _P, _P, _P, _P, _P, _P],
+                "or_second_moment": [_P, _P, _P, C.c_uint32, C.c_int, _P, _P, _P, _P, _P, _P, _P],
+                "or_adam": [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double,
+                            C.c_double, C.c_double, C.c_double],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -364,3 +367,34 @@ def derive_pixels(cfg, cam, g0, g1, gam, reinit=None):
     _load().or_derive_pixels(C.byref(cfg), C.byref(cam), _ptr(g0), _ptr(g1), _ptr(gam),
                              _ptr(rein), _ptr(out))
     return out[:, :7]
+
+
+def theta_from_gamma(cfg, gam):
+    """Regularised (mu_x, mu_y, s_xx, s_yy, s_xy) and the stored pi: [HW, 6]."""
+    gam = _f64(gam, (-1, 8))
+    return np.concatenate([derive(cfg, gam), gam[:, 5:6]], 1)
+
+
+def second_moment(cfg, cam, field, frame, n, g0, g1, theta0, theta=None):
+    """Loss [HW], gradient [HW, 6] and smallest decision margin [HW] of the
+    second-moment loss with n draws per pixel from theta0 held fixed."""
+    hw = cfg.width * cfg.height
+    g0, g1 = _f32(g0, (hw, 4)), _f32(g1, (hw, 4))
+    t0 = _f64(theta0, (hw, 6))
+    t = None if theta is None else _f64(theta, (hw, 6))
+    loss, grad, margin = np.empty(hw), np.empty((hw, 6)), np.empty(hw)
+    _load().or_second_moment(C.byref(cfg), C.byref(cam), C.byref(field), int(frame) & 0xFFFFFFFF, int(n),
+                             _ptr(g0), _ptr(g1), _ptr(t0), _ptr(t), _ptr(loss), _ptr(grad), _ptr(margin))
+    return loss, grad, margin
+
+
+def adam(cfg, gam, grad, m, v, lr, b1, b2, eps, step):
+    """One projected Adam step on theta; returns (gamma, m, v)."""
+    gam = _f64(gam, (-1, 8)).copy()
+    n = len(gam)
+    grad = _f64(grad, (n, 6))
+    m, v = _f64(m, (n, 6)).copy(), _f64(v, (n, 6)).copy()
+    c1, c2 = 1.0 / (1.0 - b1 ** step), 1.0 / (1.0 - b2 ** step)
+    _load().or_adam(C.byref(cfg), n, _ptr(gam), _ptr(grad), _ptr(m), _ptr(v), float(lr), float(b1),
+                    float(b2), float(eps), c1, c2)
+    return gam, m, v

@@ -659,6 +659,52 @@ static void eval_local(const or_field *fld, const pixel_ctx *p, const double wl[
     *pmix = p->pi_eff * *pg + (1.0 - p->pi_eff * p->Z) * *pb;
 }
 
+/* One direction drawn from the mixture of pixel p: Philox counter (pixel,
+ * frame, sample, stream0) for the strategy and Box-Muller / BRDF words,
+ * (.., stream0 + 1) for a fallback. Returns the strategy; writes the local
+ * direction, whether it is valid, the square point when the guide drew it,
+ * and the distance of the draw's decisions to their thresholds. */
+static int draw_direction(const pixel_ctx *p, const uint32_t key[2], uint32_t pix, uint32_t frame,
+                          uint32_t s, uint32_t stream0, double wl[3], double u[2], int *have_u,
+                          int *valid, double *margin)
+{
+    uint32_t c0[4] = {pix, frame, s, stream0}, r0[4];
+    uint32_t c1[4] = {pix, frame, s, stream0 + 1u}, r1[4];
+    float pi_dec = (float)p->pi_eff; /* the strategy decision is taken in binary32 */
+    or_philox(c0, key, r0);
+    double zeta = unif(r0[0]);
+    int strat;
+    *have_u = 0;
+    *margin = fabs(zeta - (double)pi_dec);
+    if (zeta < (double)pi_dec) {
+        double x1 = unif_open0(r0[1]), x2 = unif(r0[2]);
+        double rr = sqrt(-2.0 * log(x1));
+        double z1 = rr * cos(2.0 * M_PI * x2), z2 = rr * sin(2.0 * M_PI * x2);
+        u[0] = p->g5[0] + p->chol[0] * z1;
+        u[1] = p->g5[1] + p->chol[1] * z1 + p->chol[2] * z2;
+        double m = fmin(fmin(fabs(u[0]), fabs(1.0 - u[0])), fmin(fabs(u[1]), fabs(1.0 - u[1])));
+        if (m < *margin) *margin = m;
+        if (u[0] >= 0.0 && u[0] <= 1.0 && u[1] >= 0.0 && u[1] <= 1.0) {
+            strat = S_GUIDE;
+            or_square_to_hemi(u, wl);
+            *valid = wl[2] > 0.0;
+            *have_u = 1;
+        } else {
+            strat = S_FALLBACK;
+            or_philox(c1, key, r1);
+            double mb;
+            *valid = or_brdf_sample(p->rough, p->wo_l, unif(r1[0]), unif(r1[1]), wl, &mb);
+            if (mb < *margin) *margin = mb;
+        }
+    } else {
+        strat = S_BRDF;
+        double mb;
+        *valid = or_brdf_sample(p->rough, p->wo_l, unif(r0[1]), unif(r0[2]), wl, &mb);
+        if (mb < *margin) *margin = mb;
+    }
+    return strat;
+}
+
 static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_field *fld,
                          uint32_t frame, int x, int y, const float *g0, const float *g1,
                          const double *gm, int reinit, or_samples *S, double *img)
@@ -668,42 +714,13 @@ static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_fi
     pixel_ctx p;
     pixel_setup(cfg, cam, x, y, g0, g1, gm, reinit, &p);
     uint32_t key[2] = {cfg->seed_lo, cfg->seed_hi};
-    float pi_dec = (float)p.pi_eff; /* the strategy decision is taken in binary32 */
     double sum = 0.0;
     for (int s = 0; s < spp; ++s) {
         int64_t o = (int64_t)s * HW + i;
-        uint32_t c0[4] = {(uint32_t)i, frame, (uint32_t)s, 0u}, r0[4];
-        uint32_t c1[4] = {(uint32_t)i, frame, (uint32_t)s, 1u}, r1[4];
-        or_philox(c0, key, r0);
-        double zeta = unif(r0[0]);
-        double wl[3], u[2], margin = fabs(zeta - (double)pi_dec);
-        int strat, valid, have_u = 0;
-        if (zeta < (double)pi_dec) {
-            double x1 = unif_open0(r0[1]), x2 = unif(r0[2]);
-            double rr = sqrt(-2.0 * log(x1));
-            double z1 = rr * cos(2.0 * M_PI * x2), z2 = rr * sin(2.0 * M_PI * x2);
-            u[0] = p.g5[0] + p.chol[0] * z1;
-            u[1] = p.g5[1] + p.chol[1] * z1 + p.chol[2] * z2;
-            double m = fmin(fmin(fabs(u[0]), fabs(1.0 - u[0])), fmin(fabs(u[1]), fabs(1.0 - u[1])));
-            if (m < margin) margin = m;
-            if (u[0] >= 0.0 && u[0] <= 1.0 && u[1] >= 0.0 && u[1] <= 1.0) {
-                strat = S_GUIDE;
-                or_square_to_hemi(u, wl);
-                valid = wl[2] > 0.0;
-                have_u = 1;
-            } else {
-                strat = S_FALLBACK;
-                or_philox(c1, key, r1);
-                double mb;
-                valid = or_brdf_sample(p.rough, p.wo_l, unif(r1[0]), unif(r1[1]), wl, &mb);
-                if (mb < margin) margin = mb;
-            }
-        } else {
-            strat = S_BRDF;
-            double mb;
-            valid = or_brdf_sample(p.rough, p.wo_l, unif(r0[1]), unif(r0[2]), wl, &mb);
-            if (mb < margin) margin = mb;
-        }
+        double wl[3], u[2], margin;
+        int valid, have_u;
+        int strat = draw_direction(&p, key, (uint32_t)i, frame, (uint32_t)s, 0u, wl, u, &have_u, &valid,
+                                   &margin);
         double fcos = 0, pg = 0, pb = 0, pmix = 0, rad, uo[2] = {-1.0, -1.0};
         if (valid) {
             eval_local(fld, &p, wl, have_u ? u : NULL, &fcos, &pg, &pb, &pmix, &rad, uo);
@@ -903,4 +920,129 @@ void or_derive_pixels(const or_config *cfg, const or_camera *cam, const float *g
             for (int k = 0; k < 5; ++k) out[8 * i + k] = p.g5[k];
             out[8 * i + 5] = p.Z; out[8 * i + 6] = p.pi_eff; out[8 * i + 7] = 0.0;
         }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Second-moment loss and its gradient: the differentiable form of the      */
+/* guide (not in the paper). theta = (mu_x, mu_y, s_xx, s_yy, s_xy, pi) of  */
+/* a pixel's guide, regularised as in the pass. n directions w_i are drawn  */
+/* from the guide at theta0 (Philox streams 2 and 3) and held fixed, so     */
+/*   l(theta) = 1/n sum_i f_i^2 / (p_theta(w_i) p_theta0(w_i)),              */
+/* which at theta = theta0 is the Monte Carlo second moment of the          */
+/* estimator F = f / p, and                                                  */
+/*   dl/dtheta = -1/n sum_i f_i^2 (dp_theta/dtheta) / (p_theta^2 p_theta0).  */
+/* With p = pi g + (1 - pi Z) p_b and g = N(u; mu, Sigma)/(2 pi):            */
+/*   dp/dpi = g - Z p_b,                                                     */
+/*   dp/dmu = pi (g Sigma^-1 d - p_b dZ/dmu),  d = u - mu,                  */
+/*   dp/dSigma = pi (g/2 (Sigma^-1 d d^T Sigma^-1 - Sigma^-1) - p_b dZ/dSigma),*/
+/* the symmetric off-diagonal entry being one parameter (counted twice).    */
+/* A gated pixel (pi_eff = 0) has a loss but no gradient.                   */
+/* Pinned by central differences of l and by the quadrature of f^2 / p.     */
+/* ------------------------------------------------------------------------ */
+static void theta_to_gamma(const double th[6], double gm[8])
+{
+    gm[G_EX] = th[0]; gm[G_EY] = th[1];
+    gm[G_EXX] = th[2] + th[0] * th[0];
+    gm[G_EYY] = th[3] + th[1] * th[1];
+    gm[G_EXY] = th[4] + th[0] * th[1];
+    gm[G_PI] = th[5]; gm[G_K] = 0.0; gm[G_W] = 0.0;
+}
+
+static void second_moment_pixel(const or_config *cfg, const or_camera *cam, const or_field *fld,
+                                uint32_t frame, int n, int x, int y, const float *g0, const float *g1,
+                                const double th0[6], const double th[6], double *loss, double grad[6],
+                                double *margin_out)
+{
+    int W = cfg->width;
+    int64_t i = (int64_t)y * W + x;
+    double gm0[8], gm[8];
+    theta_to_gamma(th0, gm0);
+    theta_to_gamma(th, gm);
+    pixel_ctx p0, p;
+    pixel_setup(cfg, cam, x, y, g0, g1, gm0, 0, &p0);
+    pixel_setup(cfg, cam, x, y, g0, g1, gm, 0, &p);
+    double dZ[5];
+    or_rect_mass_grad(p.g5, dZ);
+    double sxx = p.g5[2], syy = p.g5[3], sxy = p.g5[4], det = sxx * syy - sxy * sxy;
+    uint32_t key[2] = {cfg->seed_lo, cfg->seed_hi};
+    double l = 0.0, gsum[6] = {0, 0, 0, 0, 0, 0}, mmin = 1.0;
+    for (int s = 0; s < n; ++s) {
+        double wl[3], u[2], margin;
+        int valid, have_u;
+        draw_direction(&p0, key, (uint32_t)i, frame, (uint32_t)s, 2u, wl, u, &have_u, &valid, &margin);
+        if (margin < mmin) mmin = margin;
+        if (!valid) continue;
+        double fcos0, pg0, pb, pmix0, rad, uo[2], fcos, pg, pmix;
+        eval_local(fld, &p0, wl, have_u ? u : NULL, &fcos0, &pg0, &pb, &pmix0, &rad, uo);
+        eval_local(fld, &p, wl, uo, &fcos, &pg, &pb, &pmix, &rad, uo);
+        if (!(fcos != 0.0) || !(pmix > 0.0) || !(pmix0 > 0.0)) continue;
+        double f2 = fcos * fcos;
+        l += f2 / (pmix * pmix0);
+        if (!(p.pi_eff > 0.0)) continue;
+        double dx = uo[0] - p.g5[0], dy = uo[1] - p.g5[1];
+        double ix = (syy * dx - sxy * dy) / det, iy = (-sxy * dx + sxx * dy) / det;
+        double dp[6];
+        dp[0] = p.pi_eff * (pg * ix - pb * dZ[0]);
+        dp[1] = p.pi_eff * (pg * iy - pb * dZ[1]);
+        dp[2] = p.pi_eff * (pg * 0.5 * (ix * ix - syy / det) - pb * dZ[2]);
+        dp[3] = p.pi_eff * (pg * 0.5 * (iy * iy - sxx / det) - pb * dZ[3]);
+        dp[4] = p.pi_eff * (pg * (ix * iy + sxy / det) - pb * dZ[4]);
+        dp[5] = pg - p.Z * pb;
+        double c = f2 / (pmix * pmix * pmix0);
+        for (int k = 0; k < 6; ++k) gsum[k] -= c * dp[k];
+    }
+    *loss = l / n;
+    for (int k = 0; k < 6; ++k) grad[k] = gsum[k] / n;
+    *margin_out = mmin;
+}
+
+/* theta0, theta: [HW][6]; theta may be NULL (= theta0). Outputs loss [HW],
+ * grad [HW][6] and the smallest decision margin of each pixel's draws. */
+void or_second_moment(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,
+                      int n, const float *g0, const float *g1, const double *theta0, const double *theta,
+                      double *loss, double *grad, double *margin)
+{
+    int W = cfg->width, H = cfg->height;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            const double *t0 = theta0 + 6 * i, *t = theta ? theta + 6 * i : t0;
+            second_moment_pixel(cfg, cam, fld, frame, n, x, y, g0, g1, t0, t, loss + i, grad + 6 * i,
+                                margin + i);
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One Adam step on theta (Kingma & Ba 2015) with projection back onto the  */
+/* guide's domain (mean in the square, variances floored, correlation       */
+/* clamped, pi clamped), written back to Gamma as moments; k and W are kept.*/
+/* gam [HW][8] in/out, grad, m, v [HW][6] (m, v in/out). c1 = 1/(1-b1^t),   */
+/* c2 = 1/(1-b2^t) are the bias corrections of step t.                     */
+/* ------------------------------------------------------------------------ */
+void or_adam(const or_config *cfg, int64_t n, double *gam, const double *grad, double *m, double *v,
+             double lr, double b1, double b2, double eps, double c1, double c2)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double *gm = gam + 8 * i, g5[5], th[6];
+        derive_gauss(cfg, gm, g5);
+        for (int k = 0; k < 5; ++k) th[k] = g5[k];
+        th[5] = gm[G_PI];
+        for (int k = 0; k < 6; ++k) {
+            double g = grad[6 * i + k];
+            m[6 * i + k] = b1 * m[6 * i + k] + (1.0 - b1) * g;
+            v[6 * i + k] = b2 * v[6 * i + k] + (1.0 - b2) * g * g;
+            th[k] -= lr * (m[6 * i + k] * c1) / (sqrt(v[6 * i + k] * c2) + eps);
+        }
+        th[0] = th[0] < 0.0 ? 0.0 : (th[0] > 1.0 ? 1.0 : th[0]);
+        th[1] = th[1] < 0.0 ? 0.0 : (th[1] > 1.0 ? 1.0 : th[1]);
+        if (th[2] < cfg->sigma2_min) th[2] = cfg->sigma2_min;
+        if (th[3] < cfg->sigma2_min) th[3] = cfg->sigma2_min;
+        double lim = cfg->rho_max * sqrt(th[2] * th[3]);
+        th[4] = th[4] > lim ? lim : (th[4] < -lim ? -lim : th[4]);
+        th[5] = th[5] < cfg->pi_min ? cfg->pi_min : (th[5] > cfg->pi_max ? cfg->pi_max : th[5]);
+        double k = gm[G_K], wmass = gm[G_W];
+        theta_to_gamma(th, gm);
+        gm[G_K] = k; gm[G_W] = wmass;
+    }
 }

@@ -67,6 +67,10 @@ _SIGNATURES = {
     "pg_get_reprojected": (C.c_int, [_P, _P]),
     "pg_check": (C.c_int, [_P]),
     "pg_philox": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int32, _P]),
+    "pg_grad": (C.c_int, [_P, C.POINTER(pg_gbuffer), C.POINTER(pg_field), C.c_uint32, C.c_int32, _P, _P, _P]),
+    "pg_adam_step": (C.c_int, [_P, _P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32]),
+    "pg_theta_from_gamma": (C.c_int, [_P, _P]),
+    "pg_theta_to_gamma": (C.c_int, [_P, _P]),
     "pg_frame_noalloc": (C.c_int, [C.POINTER(pg_config), C.POINTER(pg_gbuffer), _P, C.POINTER(pg_field), C.c_uint32,
                                    _P, _P, C.POINTER(pg_samples), _P, _P]),
     "pg_last_error": (C.c_char_p, [_P]),

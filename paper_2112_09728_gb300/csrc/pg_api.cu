@@ -21,6 +21,8 @@ struct pg_ctx {
     float4* work = nullptr;   // binary32 work copy of the staged pass
     int phase = 0;            // 1 between pg_reproject and pg_update
     int* d_err = nullptr;     // device flag: non-finite Gamma stored
+    float* adam_m = nullptr;  // Adam moments of theta, [6][H*W] each (allocated on first use)
+    float* adam_v = nullptr;
     pgk::Params base;         // configuration part of the launch parameters
     std::string err;
 };
@@ -306,6 +308,67 @@ pg_status pg_philox(const uint32_t* d_ctr, const uint32_t key[2], int64_t n, uin
     return e == cudaSuccess ? PG_OK : PG_ERR_CUDA;
 }
 
+pg_status pg_grad(pg_ctx* c, const pg_gbuffer* cur, const pg_field* field, uint32_t frame, int32_t n_samples,
+                  const float* d_theta, float* d_loss, float* d_grad) {
+    if (!c) return PG_ERR_ARG;
+    if (c->phase != 0) return fail(c, PG_ERR_STATE, "pg_grad: a staged frame is in progress");
+    pg_status s = check_gbuffer(c, cur);
+    if (s != PG_OK) return s;
+    if (n_samples < 1 || n_samples > 1 << 16) return fail(c, PG_ERR_ARG, "pg_grad: n_samples outside [1, 65536]");
+    if (!d_loss || !d_grad) return fail(c, PG_ERR_ARG, "pg_grad: d_loss and d_grad are required");
+    pgk::Params P = c->base;
+    if ((s = fill_camera(c, cur->camera, P)) != PG_OK || (s = fill_field(c, field, P)) != PG_OK) return s;
+    cudaError_t e = pgk::launch_grad(c->cfg.gamma_dtype, P, c->gam[c->cur], d_theta, (const float4*)cur->g0,
+                                     (const float4*)cur->g1, frame, n_samples, d_loss, d_grad, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pg_grad");
+    return PG_OK;
+}
+
+pg_status pg_adam_step(pg_ctx* c, const float* d_grad, float lr, float beta1, float beta2, float eps, int32_t step) {
+    if (!c) return PG_ERR_ARG;
+    if (c->phase != 0) return fail(c, PG_ERR_STATE, "pg_adam_step: a staged frame is in progress");
+    if (!d_grad) return fail(c, PG_ERR_ARG, "pg_adam_step: d_grad is required");
+    if (step < 1 || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) ||
+        !std::isfinite(lr))
+        return fail(c, PG_ERR_ARG, "pg_adam_step: need step >= 1, 0 <= beta < 1, eps > 0, finite lr");
+    const size_t bytes = 6 * hw_of(c) * sizeof(float);
+    if (!c->adam_m) {
+        if (cudaMalloc(&c->adam_m, bytes) != cudaSuccess || cudaMalloc(&c->adam_v, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            if (c->adam_m) cudaFree(c->adam_m);
+            c->adam_m = c->adam_v = nullptr;
+            return fail(c, PG_ERR_OOM, "pg_adam_step: cannot allocate the Adam moments");
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (step == 1) {   // a new run of steps starts from zero moments
+        e = cudaMemsetAsync(c->adam_m, 0, bytes, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_v, 0, bytes, c->stream);
+    }
+    const float c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, step)));
+    const float c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, step)));
+    if (e == cudaSuccess)
+        e = pgk::launch_adam(c->cfg.gamma_dtype, c->base, c->gam[c->cur], d_grad, c->adam_m, c->adam_v, lr, beta1,
+                             beta2, eps, c1, c2, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pg_adam_step");
+    return PG_OK;
+}
+
+pg_status pg_theta_from_gamma(pg_ctx* c, float* d_theta) {
+    if (!c || !d_theta) return fail(c, PG_ERR_ARG, "pg_theta_from_gamma: NULL argument");
+    cudaError_t e = pgk::launch_theta_get(c->cfg.gamma_dtype, c->base, c->gam[c->cur], d_theta, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pg_theta_from_gamma");
+    return PG_OK;
+}
+
+pg_status pg_theta_to_gamma(pg_ctx* c, const float* d_theta) {
+    if (!c || !d_theta) return fail(c, PG_ERR_ARG, "pg_theta_to_gamma: NULL argument");
+    if (c->phase != 0) return fail(c, PG_ERR_STATE, "pg_theta_to_gamma: a staged frame is in progress");
+    cudaError_t e = pgk::launch_theta_set(c->cfg.gamma_dtype, c->base, c->gam[c->cur], d_theta, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pg_theta_to_gamma");
+    return PG_OK;
+}
+
 const char* pg_last_error(const pg_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
 
 void pg_destroy(pg_ctx* c) {
@@ -315,6 +378,8 @@ void pg_destroy(pg_ctx* c) {
         if (c->gam[b]) cudaFree(c->gam[b]);
     if (c->work) cudaFree(c->work);
     if (c->d_err) cudaFree(c->d_err);
+    if (c->adam_m) cudaFree(c->adam_m);
+    if (c->adam_v) cudaFree(c->adam_v);
     delete c;
 }
 

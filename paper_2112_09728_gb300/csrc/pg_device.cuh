@@ -582,14 +582,15 @@ __device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, con
     }
 }
 
-// Random numbers: word 0 of Philox stream 0 picks the strategy; words 1 and 2
-// drive Box-Muller for a guide draw or the BRDF draw otherwise (independent of
-// word 0, hence still uniform given the choice); a guide draw that left the
-// square takes its BRDF draw from stream 1.
+// Random numbers: word 0 of Philox stream `stream0` (0 for the pass, 2 for the
+// adjoint's draws) picks the strategy; words 1 and 2 drive Box-Muller for a
+// guide draw or the BRDF draw otherwise (independent of word 0, hence still
+// uniform given the choice); a guide draw that left the square takes its BRDF
+// draw from stream `stream0 + 1`.
 __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, const Surf& s, uint32_t pix,
-                                           uint32_t frame, uint32_t si) {
+                                           uint32_t frame, uint32_t si, uint32_t stream0 = 0u) {
     Smp o;
-    const uint4 r0 = philox4x32_10(make_uint4(pix, frame, si, 0u), P.key0, P.key1);
+    const uint4 r0 = philox4x32_10(make_uint4(pix, frame, si, stream0), P.key0, P.key1);
     const float zeta = unit24(r0.x);
     bool have_u = false, valid;
     if (zeta < d.pi_eff) {
@@ -607,7 +608,7 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
             have_u = true;
         } else {
             o.strat = ST_FALLBACK;
-            const uint4 r1 = philox4x32_10(make_uint4(pix, frame, si, 1u), P.key0, P.key1);
+            const uint4 r1 = philox4x32_10(make_uint4(pix, frame, si, stream0 + 1u), P.key0, P.key1);
             valid = brdf_sample(s, unit24(r1.x), unit24(r1.y), o.wl);
         }
     } else {
@@ -617,6 +618,38 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
     if (!valid) o.strat |= ST_INVALID;
     eval_sample(P, d, s, o, have_u);
     return o;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of Z with respect to (mu_x, mu_y, s_xx, s_yy, s_xy), from the
+// corner form of Z and the bivariate normal cdf's derivatives
+//   dPhi2/dh = phi(h) Phi((k - rho h)/sqrt(1-rho^2)),
+//   dPhi2/dk = phi(k) Phi((h - rho k)/sqrt(1-rho^2)),
+//   dPhi2/drho = exp(-(h^2 - 2 rho h k + k^2)/(2(1-rho^2))) / (2 pi sqrt(1-rho^2)),
+// chained through h = (a - mu_x)/s_x, k = (b - mu_y)/s_y, rho = s_xy/(s_x s_y).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float normal_cdf(float x) { return 0.5f * erfcf(-x * 0.70710678118654752f); }
+
+__device__ __forceinline__ void rect_mass_grad(const Guide& d, float dz[5]) {
+    const float isx = d.il11, isy = rsqrtf(d.syy);
+    const float rho = d.sxy * isx * isy;
+    const float om = fmaf(-rho, rho, 1.0f), ir1 = rsqrtf(om);
+    const float c0 = 0.398942280401432678f;      // 1 / sqrt(2 pi)
+    for (int k = 0; k < 5; ++k) dz[k] = 0.0f;
+#pragma unroll
+    for (int cn = 0; cn < 4; ++cn) {
+        const float a = (float)(cn & 1), b = (float)(cn >> 1);
+        const float sg = (cn == 0 || cn == 3) ? 1.0f : -1.0f;
+        const float h = (a - d.mx) * isx, k = (b - d.my) * isy;
+        const float dh = c0 * __expf(-0.5f * h * h) * normal_cdf((k - rho * h) * ir1);
+        const float dk = c0 * __expf(-0.5f * k * k) * normal_cdf((h - rho * k) * ir1);
+        const float dr = kInv2Pi * ir1 * __expf(-0.5f * (h * h - 2.0f * rho * h * k + k * k) / om);
+        dz[0] -= sg * dh * isx;
+        dz[1] -= sg * dk * isy;
+        dz[2] -= sg * (dh * h + dr * rho) * 0.5f * isx * isx;
+        dz[3] -= sg * (dk * k + dr * rho) * 0.5f * isy * isy;
+        dz[4] += sg * dr * isx * isy;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -31,6 +31,12 @@ cudaError_t launch_to_f32(int dt, const Params& P, const void* src, bool src_is_
                           cudaStream_t st);
 cudaError_t launch_from_f32(int dt, const Params& P, const float4* src, void* dst, cudaStream_t st);
 
+cudaError_t launch_grad(int dt, const Params& P, const void* gam, const float* theta, const float4* g0,
+                        const float4* g1, uint32_t frame, int n, float* loss, float* grad, cudaStream_t st);
+cudaError_t launch_adam(int dt, const Params& P, void* gam, const float* grad, float* m, float* v, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t st);
+cudaError_t launch_theta_get(int dt, const Params& P, const void* gam, float* theta, cudaStream_t st);
+cudaError_t launch_theta_set(int dt, const Params& P, void* gam, const float* theta, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out, bool curand,
                           cudaStream_t st);
 

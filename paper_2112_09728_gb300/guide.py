@@ -178,6 +178,36 @@ class GuidePass:
         o = out.view(7, n, self.hw)
         return {k: o[j] for j, k in enumerate(EVAL_KEYS)}
 
+    def pg_grad(self, g0, g1, camera, field, frame, n_samples, theta=None, loss=None, grad=None):
+        """Second-moment loss [H*W] and its gradient [6, H*W] at theta (default:
+        the current Gamma's), n_samples draws per pixel."""
+        if theta is not None:
+            self._check_len(theta, 6 * self.hw, "theta")
+        if loss is None:
+            loss = torch.empty(self.hw, dtype=torch.float32, device="cuda")
+        if grad is None:
+            grad = torch.empty((6, self.hw), dtype=torch.float32, device="cuda")
+        self._call("pg_grad", C.byref(self._gbuf(g0, g1, camera)), C.byref(make_field(field)),
+                   C.c_uint32(int(frame) & 0xFFFFFFFF), C.c_int32(int(n_samples)),
+                   C.c_void_p(_ptr(theta, what="theta")), C.c_void_p(_ptr(loss, what="loss")),
+                   C.c_void_p(_ptr(grad, what="grad")))
+        return loss, grad
+
+    def pg_adam_step(self, grad, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, step=1):
+        self._check_len(grad, 6 * self.hw, "grad")
+        self._call("pg_adam_step", C.c_void_p(_ptr(grad, what="grad")), C.c_float(lr), C.c_float(beta1),
+                   C.c_float(beta2), C.c_float(eps), C.c_int32(int(step)))
+
+    def pg_theta_from_gamma(self, theta=None):
+        if theta is None:
+            theta = torch.empty((6, self.hw), dtype=torch.float32, device="cuda")
+        self._call("pg_theta_from_gamma", C.c_void_p(_ptr(theta, what="theta")))
+        return theta
+
+    def pg_theta_to_gamma(self, theta):
+        self._check_len(theta, 6 * self.hw, "theta")
+        self._call("pg_theta_to_gamma", C.c_void_p(_ptr(theta, what="theta")))
+
     def gamma_bytes(self):
         return int(self._lib.pg_gamma_bytes(self._h))
 
@@ -271,3 +301,20 @@ def planes_to_rows(planes):
 
 def rows_to_planes(rows):
     return torch.stack([rows[:, :4], rows[:, 4:]], 0).contiguous()
+
+
+class PgSecondMoment(torch.autograd.Function):
+    """Per-pixel Monte Carlo second moment of the guided estimator as a
+    function of theta [6, H*W]; forward and backward both come from pg_grad's
+    kernel (the draws are held fixed, so the gradient is exact for them)."""
+
+    @staticmethod
+    def forward(ctx, theta, guide, g0, g1, camera, field, frame, n_samples):
+        loss, grad = guide.pg_grad(g0, g1, camera, field, frame, n_samples, theta=theta.detach().contiguous())
+        ctx.save_for_backward(grad)
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        (grad,) = ctx.saved_tensors
+        return grad_loss[None, :] * grad, None, None, None, None, None, None, None

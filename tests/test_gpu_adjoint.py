@@ -1,0 +1,101 @@
+"""The differentiable form: the second-moment loss, its hand-written adjoint,
+the projected Adam step and the torch.autograd wrapper, against the oracle.
+
+Tolerances: the GPU draws its own binary32 directions, so the loss and the
+gradient agree with the oracle's (whose gradient is pinned by central
+differences on the CPU) to 1e-3 relative per component, with a floor of
+1e-3 of the pixel's largest component; pixels with a draw within 1e-5 of a
+decision threshold are excluded. Adam from identical inputs agrees to
+1e-5 relative + 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_09728_gb300 import scenes
+
+from _pg import close, dev, get_gamma_rows, guide, host, ocam, ocfg, ofld, set_gamma_rows
+
+pytestmark = pytest.mark.gpu
+
+
+def _theta(rng, hw):
+    sx, sy = np.exp(rng.uniform(np.log(0.04), np.log(0.25), (2, hw)))
+    th = np.stack([rng.uniform(0.2, 0.8, hw), rng.uniform(0.2, 0.8, hw), sx * sx, sy * sy,
+                   rng.uniform(-0.7, 0.7, hw) * sx * sy, rng.uniform(0.2, 0.8, hw)], 1)
+    return th.astype(np.float32)
+
+
+def _case(seed=61, W=41, H=23):
+    rng = np.random.default_rng(seed)
+    g0, g1 = scenes.random_gbuffer(rng, W, H, ggx_frac=0.5, rough_lo=0.25, max_tilt=0.4)
+    par = scenes.Params(W, H, seed=seed * 13)
+    cam = scenes.top_down_camera(pixel_size=0.3)
+    fld = scenes.masked_lobe_field(seed, n_lobes=3, kappa_lo=5.0, kappa_hi=60.0, constant=0.1)
+    return rng, par, cam, fld, g0, g1
+
+
+def test_adjoint_matches_oracle():
+    rng, par, cam, fld, g0, g1 = _case()
+    hw = par.width * par.height
+    th = _theta(rng, hw)
+    n = 64
+    gp = guide(par)
+    loss, grad = gp.pg_grad(dev(g0), dev(g1), cam, fld, 7, n, theta=dev(np.ascontiguousarray(th.T)))
+    loss, grad = host(loss).astype(np.float64), host(grad).T.astype(np.float64)
+    rl, rg, margin = O.second_moment(ocfg(par), ocam(cam), ofld(fld), 7, n, g0, g1, th.astype(np.float64))
+    ok = margin > 1e-5
+    assert ok.mean() > 0.9
+    assert close(loss[ok], rl[ok], 1e-3, 1e-9) <= 1.0
+    floor = 1e-3 * np.abs(rg).max(1, keepdims=True)
+    lim = 1e-3 * np.maximum(np.abs(rg), floor) + 1e-12
+    assert (np.abs(grad - rg)[ok] <= lim[ok]).all(), np.max((np.abs(grad - rg) / lim)[ok])
+    gated = (g1[:, 2] >= 0) & (g1[:, 2] < par.rough_min)
+    assert (grad[gated] == 0).all()
+
+
+def test_adjoint_from_gamma_equals_adjoint_from_theta():
+    rng, par, cam, fld, g0, g1 = _case(62)
+    hw = par.width * par.height
+    th = dev(np.ascontiguousarray(_theta(rng, hw).T))
+    gp = guide(par)
+    gp.pg_theta_to_gamma(th)
+    back = gp.pg_theta_from_gamma()
+    assert close(host(back), host(th), 1e-6, 1e-7) <= 1.0
+    l1, g1_ = gp.pg_grad(dev(g0), dev(g1), cam, fld, 2, 32)
+    l2, g2_ = gp.pg_grad(dev(g0), dev(g1), cam, fld, 2, 32, theta=back)
+    assert close(host(l1), host(l2), 1e-6, 1e-9) <= 1.0
+    assert close(host(g1_), host(g2_), 1e-5, 1e-9) <= 1.0
+
+
+def test_adam_steps_match_oracle():
+    rng, par, cam, fld, g0, g1 = _case(63)
+    hw = par.width * par.height
+    gam = scenes.random_gamma(rng, hw, k_hi=32)
+    gp = guide(par)
+    set_gamma_rows(gp, gam)
+    cfg = ocfg(par)
+    ref = gam.astype(np.float64)
+    m = v = np.zeros((hw, 6))
+    for step in (1, 2, 3):
+        grad = rng.normal(size=(hw, 6)).astype(np.float32) * np.array([1, 1, 50, 50, 50, 1], np.float32)
+        gp.pg_adam_step(dev(np.ascontiguousarray(grad.T)), lr=1e-2, step=step)
+        ref, m, v = O.adam(cfg, ref, grad.astype(np.float64), m, v, 1e-2, 0.9, 0.999, 1e-8, step)
+    got = get_gamma_rows(gp)
+    assert close(got, ref, 1e-5, 1e-6) <= 1.0
+
+
+def test_autograd_function_backward_is_the_adjoint():
+    import torch
+    from paper_2112_09728_gb300.guide import PgSecondMoment
+    rng, par, cam, fld, g0, g1 = _case(64)
+    hw = par.width * par.height
+    th = dev(np.ascontiguousarray(_theta(rng, hw).T)).requires_grad_(True)
+    gp = guide(par)
+    G0, G1 = dev(g0), dev(g1)
+    loss = PgSecondMoment.apply(th, gp, G0, G1, cam, fld, 3, 16)
+    w = torch.linspace(0.5, 1.5, hw, device="cuda")
+    (loss * w).sum().backward()
+    l_ref, g_ref = gp.pg_grad(G0, G1, cam, fld, 3, 16, theta=th.detach())
+    assert torch.equal(loss.detach(), l_ref)
+    assert torch.allclose(th.grad, w[None, :] * g_ref, rtol=1e-6, atol=0)

@@ -1,0 +1,138 @@
+"""The reduced-precision form of the pass: Gamma stored in FP16 or BF16 as
+{mu_x, mu_y, s_xx, s_yy, s_xy, pi, k, W} (mean and central second moments),
+all arithmetic in binary32 with Kahan-compensated E-step sums.
+
+* One frame from a Gamma that is exactly representable in the storage type:
+  the GPU computes in binary32 and rounds once; the oracle computes in binary64
+  and the test rounds once to the same type. The two may differ where the
+  binary32 result lies within ~1e-6 of a rounding boundary, so the bound is one
+  unit in the last place of the storage type.
+* The 64x64, 8-frame workload in FP32, FP16 and BF16 against the FP64 oracle:
+  per-parameter error and image MSE are reported and bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_09728_gb300 import scenes
+
+from _pg import close, dev, get_gamma_rows, guide, host, ocam, ocfg, ofld, set_gamma_rows
+
+pytestmark = pytest.mark.gpu
+
+
+def _round(x, dtype):
+    import torch
+    t = torch.from_numpy(np.asarray(x, np.float64))
+    return (t.to(torch.float16) if dtype == "f16" else t.to(torch.bfloat16)).to(torch.float64).numpy()
+
+
+def _ulp(x, dtype):
+    """Unit in the last place of the storage type at |x| (subnormal floor)."""
+    mant = 10 if dtype == "f16" else 7
+    tiny = 2.0 ** -24 if dtype == "f16" else 2.0 ** -133
+    e = np.floor(np.log2(np.maximum(np.abs(x), 1e-300)))
+    return np.maximum(2.0 ** (e - mant), tiny)
+
+
+def _record_bytes(central, dtype):
+    """[HW, 8] central-form rows -> raw 16-byte records (uint8 [HW*16])."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(central, np.float64))
+    h = t.to(torch.float16) if dtype == "f16" else t.to(torch.bfloat16)
+    return h.contiguous().view(torch.uint8).reshape(-1).numpy()
+
+
+def _records_to_central(raw, dtype):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(raw)).view(torch.float16 if dtype == "f16" else torch.bfloat16)
+    return t.to(torch.float64).numpy().reshape(-1, 8)
+
+
+def _central_to_raw_moments(c):
+    mx, my, sxx, syy, sxy = c[:, 0], c[:, 1], c[:, 2], c[:, 3], c[:, 4]
+    return np.stack([mx, my, sxx + mx * mx, syy + my * my, sxy + mx * my, c[:, 5], c[:, 6], c[:, 7]], 1)
+
+
+def _raw_to_central(r):
+    mx, my = r[:, 0], r[:, 1]
+    return np.stack([mx, my, r[:, 2] - mx * mx, r[:, 3] - my * my, r[:, 4] - mx * my, r[:, 5], r[:, 6], r[:, 7]], 1)
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_reduced_precision_frame_matches_oracle_to_one_ulp(dtype):
+    import torch
+    W, H, spp = 40, 27, 2
+    rng = np.random.default_rng(31)
+    g0, g1 = scenes.random_gbuffer(rng, W, H, rough_lo=0.05)
+    hw = W * H
+    mx, my = rng.uniform(0.05, 0.95, (2, hw))
+    sx, sy = np.exp(rng.uniform(np.log(0.03), np.log(0.4), (2, hw)))
+    rho = rng.uniform(-0.8, 0.8, hw)
+    cen = np.stack([mx, my, sx * sx, sy * sy, rho * sx * sy, rng.uniform(0.05, 0.95, hw),
+                    rng.integers(0, 33, hw).astype(float), rng.uniform(0.1, 3.0, hw)], 1)
+    cen = _round(cen, dtype)                     # exactly representable in storage
+    par = scenes.Params(W, H, spp=spp, seed=4242)
+    cam = scenes.top_down_camera(pixel_size=0.5)
+    fld = scenes.masked_lobe_field(9, n_lobes=3, kappa_hi=150.0, constant=0.05)
+    gp = guide(par, dtype)
+    gp.pg_set_gamma(torch.from_numpy(_record_bytes(cen, dtype)).cuda())
+    img = torch.empty(hw, device="cuda")
+    gp.pg_frame(dev(g0), dev(g1), cam, dev(g0), fld, 1, img)
+    gp.pg_check()
+    got = _records_to_central(host(gp.pg_get_gamma()), dtype)
+    ref_raw, _, s, rimg = O.frame(ocfg(par), ocam(cam), ofld(fld), 1, g0, g1, g0, _central_to_raw_moments(cen))
+    ref = _round(_raw_to_central(ref_raw), dtype)
+    ok = ~(s["margin"] < 1e-5).reshape(spp, -1).any(0)
+    assert ok.mean() > 0.99
+    d = np.abs(got - ref)[ok]
+    assert (d <= 1.01 * _ulp(ref[ok], dtype)).all(), np.max(d / _ulp(ref[ok], dtype))
+    assert (got[ok, 6] == ref[ok, 6]).all()
+    assert close(host(img)[ok], rimg[ok], 1e-4, 1e-6) <= 1.0
+
+
+def test_precision_report_small_workload():
+    """64x64, 1 spp, 8 frames: each storage form against the FP64 oracle run
+    forward on its own, and FP16/BF16 against the FP32 pass."""
+    import torch
+    wl = scenes.workload_small()
+    par, cam, fld = wl["params"], wl["camera"], wl["field"]
+    g0, g1, g0p = wl["gbuf"](0)
+    cfg = ocfg(par)
+    ref = O.init_gamma(cfg, par.width * par.height, pi=par.init_pi)
+    imgs_ref = []
+    amb = np.zeros(par.width * par.height, bool)
+    for t in range(wl["frames"]):
+        ref, _, s, rimg = O.frame(cfg, ocam(cam), ofld(fld), t, g0, g1, g0p, ref)
+        amb |= (s["margin"] < 1e-5).reshape(par.spp, -1).any(0)
+        imgs_ref.append(rimg)
+    ok = ~amb                 # pixels whose decisions never came within 1e-5 of a threshold
+    out = {}
+    for dtype in ("f32", "f16", "bf16"):
+        gp = guide(par, dtype)
+        img = torch.empty(par.width * par.height, device="cuda")
+        imgs = []
+        for t in range(wl["frames"]):
+            gp.pg_frame(dev(g0), dev(g1), cam, dev(g0p), fld, t, img)
+            imgs.append(host(img).astype(np.float64))
+        gp.pg_check()
+        out[dtype] = (_raw_to_central(get_gamma_rows(gp)), np.array(imgs))
+    rc = _raw_to_central(ref)
+    names = ("mu_x", "mu_y", "s_xx", "s_yy", "s_xy", "pi", "k", "W")
+    report = {}
+    for dtype, (c, im) in out.items():
+        d = np.abs(c - rc)[ok]
+        err, err99 = d.max(0), np.percentile(d, 99, axis=0)
+        mse = float(((im - np.array(imgs_ref))[:, ok] ** 2).mean())
+        report[dtype] = (err, err99, mse)
+        print(dtype, "vs FP64 oracle: max |err|", dict(zip(names, np.round(err, 7))), "99th pct",
+              dict(zip(names, np.round(err99, 7))), "image MSE:", mse)
+    for dtype in ("f16", "bf16"):
+        e = np.abs(out[dtype][0] - out["f32"][0])[ok].max(0)
+        print(dtype, "max |err| vs FP32 pass:", dict(zip(names, np.round(e, 7))))
+    # FP32 tracks the oracle closely. In FP16/BF16 the stored pi differs from
+    # the FP64 one by a storage ulp, so a few strategy choices flip and those
+    # pixels take other samples: their bound is on the 99th percentile.
+    assert report["f32"][0][:6].max() < 2e-4
+    assert report["f16"][1][:6].max() < 5e-3
+    assert report["bf16"][1][:6].max() < 5e-2

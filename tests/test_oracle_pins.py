@@ -592,3 +592,82 @@ def test_reinit_pixel_samples_brdf_only():
     assert ((s["strategy"] & 3) == 0).all()
     s2, _ = O.sample(cfg, cam, fld, 0, g0, g1, gam)
     assert ((s2["strategy"] & 3) != 0).mean() > 0.8
+
+
+# ---------------------------------------------------------------------------
+# Second-moment loss and its gradient (the differentiable form)
+# ---------------------------------------------------------------------------
+def _adjoint_case(n_pix=24, seed=41, rough_frac=0.5):
+    rng = np.random.default_rng(seed)
+    cfg = O.make_config(n_pix, 1, seed=seed)
+    cam = O.make_camera(0, (0, 0, 5), (0, 0, -1), (1, 0, 0), (0, 1, 0))
+    fld = O.make_field([[0.3, 0.2, 0.93], [-0.5, 0.1, 0.86]], [15.0, 40.0], [1.0, 0.7], constant=0.1)
+    g0, g1 = scenes.random_gbuffer(rng, n_pix, 1, ggx_frac=rough_frac, rough_lo=0.3, max_tilt=0.3)
+    th = np.stack([rng.uniform(0.25, 0.75, n_pix), rng.uniform(0.25, 0.75, n_pix),
+                   rng.uniform(0.004, 0.03, n_pix), rng.uniform(0.004, 0.03, n_pix),
+                   np.zeros(n_pix), rng.uniform(0.2, 0.8, n_pix)], 1)
+    th[:, 4] = rng.uniform(-0.6, 0.6, n_pix) * np.sqrt(th[:, 2] * th[:, 3])
+    return cfg, cam, fld, g0, g1, th
+
+
+def test_second_moment_gradient_matches_central_differences():
+    cfg, cam, fld, g0, g1, th = _adjoint_case()
+    n = 32
+    loss, grad, _ = O.second_moment(cfg, cam, fld, 3, n, g0, g1, th)
+    scale = np.abs(th).max(0) * 0 + np.array([1, 1, 0.01, 0.01, 0.01, 1.0])
+    for j in range(6):
+        h = 1e-5 * scale[j]
+        def at(d):
+            t = th.copy()
+            t[:, j] += d
+            return O.second_moment(cfg, cam, fld, 3, n, g0, g1, th, t)[0]
+        # Richardson-extrapolated central difference
+        d1 = (at(h) - at(-h)) / (2 * h)
+        d2 = (at(2 * h) - at(-2 * h)) / (4 * h)
+        fd = (4 * d1 - d2) / 3
+        ref = np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max())
+        assert np.abs(grad[:, j] - fd).max() / ref.max() < 1e-6 or (np.abs(grad[:, j] - fd) / ref).max() < 1e-5, j
+
+
+def test_second_moment_loss_is_the_estimators_second_moment():
+    """At theta = theta0 the loss is the Monte Carlo second moment of F; over
+    many replicas it converges to the integral of f^2 / p over the hemisphere."""
+    reps, n = 256, 16
+    cfg = O.make_config(reps, 1, seed=5)
+    cam = O.make_camera(0, (0, 0, 5), (0, 0, -1), (1, 0, 0), (0, 1, 0))
+    fld = O.make_field([[0.3, 0.2, 0.93]], [20.0], [1.0], constant=0.1)
+    g0 = np.tile(np.array([[0, 0, 1, 5.0]], np.float32), (reps, 1))
+    g1 = np.tile(np.array([[0, 0, -1, 0.8]], np.float32), (reps, 1))
+    th = np.tile([0.6, 0.55, 0.01, 0.02, 0.004, 0.5], (reps, 1))
+    loss, _, _ = O.second_moment(cfg, cam, fld, 0, n, g0, g1, th)
+    m = 600
+    gr = (np.arange(m) + 0.5) / m
+    U, V = np.meshgrid(gr, gr)
+    dirs = O.square_to_hemi(np.stack([U.ravel(), V.ravel()], 1))
+    gam = np.array([[0.6, 0.55, 0.01 + 0.36, 0.02 + 0.3025, 0.004 + 0.33, 0.5, 0, 0]])
+    c1 = O.make_config(1, 1)
+    ev = O.evaluate(c1, cam, fld, g0[:1], g1[:1], gam, dirs[:, None, :])
+    ok = ev["pmix"] > 0
+    ref = 2 * np.pi * np.where(ok, ev["fcos"] ** 2 / np.where(ok, ev["pmix"], 1), 0).mean()
+    assert abs(loss.mean() - ref) < 4 * loss.std() / np.sqrt(reps)
+
+
+def test_adam_first_step_closed_form_and_projection():
+    cfg = O.make_config(3, 1)
+    gam = np.array([[0.5, 0.5, 0.26, 0.27, 0.251, 0.5, 4, 2.0],
+                    [0.9995, 0.2, 0.9995 ** 2 + 0.01, 0.05, 0.2 * 0.9995, 0.0505, 7, 1.0],
+                    [0.3, 0.7, 0.09 + 0.02, 0.49 + 0.02, 0.21, 0.9, 1, 0.5]])
+    grad = np.array([[1.0, -2.0, 0.5, -0.5, 1e-3, -1.0],
+                     [-3.0, 1.0, 1.0, 1.0, 1.0, 5e3],
+                     [0.0, 0.0, 0.0, 0.0, 0.0, 0.0]])
+    th0 = O.theta_from_gamma(cfg, gam)
+    out, m, v = O.adam(cfg, gam, grad, np.zeros((3, 6)), np.zeros((3, 6)), 1e-3, 0.9, 0.999, 1e-8, 1)
+    th1 = O.theta_from_gamma(cfg, out)
+    # pixel 0: interior; at step 1 the bias-corrected moments are g and g^2, so
+    # every parameter moves by lr g / (|g| + eps) against the gradient
+    assert np.allclose(th1[0], th0[0] - 1e-3 * grad[0] / (np.abs(grad[0]) + 1e-8), atol=1e-12)
+    # pixel 1: the mean hits the square's edge and pi its lower clamp
+    assert th1[1, 0] == 1.0 and th1[1, 5] == pytest.approx(0.05, rel=1e-6)
+    # pixel 2: zero gradient, zero step
+    assert np.allclose(th1[2], th0[2], atol=1e-12)
+    assert (out[:, 6:] == gam[:, 6:]).all()      # k and W are kept
