@@ -207,7 +207,11 @@ static double simpson_rec(fn1 f, const void *c, double a, double b, double fa, d
     double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm);
     double right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
     double delta = left + right - whole;
-    if (depth <= 0 || fabs(delta) <= 15.0 * eps) return left + right + delta / 15.0;
+    /* stop at the requested absolute error, or at 1e-14 of the piece itself:
+     * binary64 cannot resolve less, and a smaller target never converges */
+    double tol = 15.0 * eps, floor_rel = 1e-14 * fabs(left + right);
+    if (tol < floor_rel) tol = floor_rel;
+    if (depth <= 0 || fabs(delta) <= tol) return left + right + delta / 15.0;
     return simpson_rec(f, c, a, m, fa, flm, fm, left, 0.5 * eps, depth - 1) +
            simpson_rec(f, c, m, b, fm, frm, fb, right, 0.5 * eps, depth - 1);
 }
@@ -218,7 +222,7 @@ static double simpson(fn1 f, const void *c, double a, double b, double eps)
     if (!(b > a)) return 0.0;
     double fa = f(a, c), fb = f(b, c), m = 0.5 * (a + b), fm = f(m, c);
     double whole = (b - a) / 6.0 * (fa + 4.0 * fm + fb);
-    return simpson_rec(f, c, a, b, fa, fm, fb, whole, eps, 40);
+    return simpson_rec(f, c, a, b, fa, fm, fb, whole, eps, 30);
 }
 
 /* Integral over [0,1] of a function with a Gaussian-shaped peak of scale s at

@@ -11,7 +11,7 @@ Layouts (all float32, one row per pixel, row-major y*W + x):
   g0 [H*W, 4]  normal x, y, z, depth (distance along the primary ray)
   g1 [H*W, 4]  motion x, y (previous minus current screen position, pixels),
                roughness (negative = Lambertian), albedo
-  gamma [H*W, 8]  E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, I
+  gamma [H*W, 8]  E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, W
 """
 from __future__ import annotations
 
@@ -265,3 +265,186 @@ def random_samples(rng, spp, hw):
     return dict(wx=d[:, 0].copy(), wy=d[:, 1].copy(), wz=d[:, 2].copy(),
                 radiance=rng.uniform(0.0, 5.0, n).astype(np.float32),
                 estimate=rng.uniform(0.0, 3.0, n).astype(np.float32), strategy=strat)
+
+
+# ----------------------------------------------------------------------------
+# Workload 5: 3840x2160 pinhole camera yawing 0.5 deg/frame over a normal-
+# mapped ground with 16 occluding quads; GGX everywhere, 8 lobes, 4 spp.
+# ----------------------------------------------------------------------------
+class _NP:
+    """numpy side of the small array interface QuadScene runs on."""
+    def __init__(self):
+        self.m = np
+    def arr(self, x): return np.asarray(x, np.float64)
+    def norm(self, x): return np.linalg.norm(x, axis=-1, keepdims=True)
+    def cross(self, a, b): return np.cross(a, b)
+    def meshgrid(self, a, b): return np.meshgrid(a, b)
+    def arange(self, n): return np.arange(n, dtype=np.float64)
+    def f32(self, x): return np.asarray(x, np.float32)
+    def i64(self, x): return x.astype(np.int64)
+    def cat(self, xs): return np.concatenate(xs, -1)
+
+
+class _TORCH:
+    """torch side (on a device) of the same interface, for large screens."""
+    def __init__(self, device):
+        import torch
+        self.m, self.t, self.dev = torch, torch, device
+    def arr(self, x): return self.t.as_tensor(np.asarray(x, np.float64), device=self.dev)
+    def norm(self, x): return self.t.linalg.norm(x, dim=-1, keepdim=True)
+    def cross(self, a, b): return self.t.linalg.cross(a, self.t.broadcast_to(b, a.shape) if b.dim() < a.dim() else b)
+    def meshgrid(self, a, b): return self.t.meshgrid(a, b, indexing="xy")
+    def arange(self, n): return self.t.arange(n, dtype=self.t.float64, device=self.dev)
+    def f32(self, x): return x.to(self.t.float32)
+    def i64(self, x): return x.to(self.t.int64)
+    def cat(self, xs): return self.t.cat(xs, -1)
+
+
+class QuadScene:
+    """Analytic ray casting of a ground plane z = 0 (normals from a spectral
+    fBm, in world units) and n_quads random rectangles above it, seen by a
+    pinhole camera that orbits the origin at radius `orbit` and height
+    cam_height, looking inward and pitched down, turning yaw_step_deg per
+    frame (so nearer quads move against farther ground: parallax and
+    disocclusion). Depth is the distance along the primary ray; motion vectors
+    come from projecting each hit point into the previous frame's camera.
+    Quads are two-sided (normals face the viewer). Roughness is drawn per
+    world cell of size 0.25 (GGX U(rough_lo, 1)), albedo 0.8. gbuffer() runs
+    in numpy; gbuffer_on(t, device) runs the same arithmetic in torch on a
+    device and returns device tensors."""
+
+    def __init__(self, width, height, seed, n_quads=16, hfov_deg=60.0, yaw_step_deg=0.5, pitch_deg=-20.0,
+                 cam_height=2.0, orbit=10.0, rough_lo=0.02):
+        self.W, self.H = width, height
+        self.yaw_step = np.radians(yaw_step_deg)
+        self.pitch = np.radians(pitch_deg)
+        self.cam_h = cam_height
+        self.orbit = orbit
+        self.rough_lo = rough_lo
+        self.tan_v = np.tan(np.radians(hfov_deg) / 2) * height / width
+        self.hf = Heightfield(seed, amplitude=0.05, period=4.0)
+        rng = np.random.default_rng(seed + 3)
+        # along the arc the camera sweeps in 120 frames, between it and the centre
+        ang = rng.uniform(-0.3, 0.3 + np.radians(yaw_step_deg) * 120, n_quads)
+        dist = rng.uniform(0.6, 0.9, n_quads) * orbit
+        self.qc = np.stack([dist * np.cos(ang), dist * np.sin(ang), rng.uniform(0.3, 1.5, n_quads)], 1)
+        e1 = rng.normal(size=(n_quads, 3))
+        e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+        e2 = np.cross(e1, rng.normal(size=(n_quads, 3)))
+        e2 /= np.linalg.norm(e2, axis=1, keepdims=True)
+        self.qe1 = e1 * rng.uniform(0.35, 1.2, (n_quads, 1))
+        self.qe2 = e2 * rng.uniform(0.35, 1.2, (n_quads, 1))
+        self.rough_seed = seed + 5
+
+    def camera(self, t):
+        phi = self.yaw_step * t
+        pos = (self.orbit * np.cos(phi), self.orbit * np.sin(phi), self.cam_h)
+        yaw = phi + np.pi
+        fwd = np.array([np.cos(yaw) * np.cos(self.pitch), np.sin(yaw) * np.cos(self.pitch), np.sin(self.pitch)])
+        right = np.cross(fwd, [0.0, 0.0, 1.0])
+        right /= np.linalg.norm(right)
+        up = np.cross(right, fwd)
+        return Camera(1, pos, tuple(fwd), tuple(right), tuple(up), tan_half_fov=float(self.tan_v))
+
+    def _rays(self, X, cam):
+        W, H, m = self.W, self.H, X.m
+        x = (X.arange(W) + 0.5) / W * 2 - 1
+        y = 1 - (X.arange(H) + 0.5) / H * 2
+        sx, sy = X.meshgrid(x * self.tan_v * W / H, y * self.tan_v)
+        f, r, u = X.arr(cam.fwd), X.arr(cam.right), X.arr(cam.up)
+        d = f + sx[..., None] * r + sy[..., None] * u
+        return d / X.norm(d)
+
+    def _cast(self, X, t):
+        m = X.m
+        cam = self.camera(t)
+        o = X.arr(cam.origin)
+        d = self._rays(X, cam)
+        inf = float("inf")
+        tg = -o[2] / d[..., 2]
+        ground = (d[..., 2] < 0) & (tg > 0)
+        tmin = m.where(ground, tg, inf * m.ones_like(tg))
+        n = m.zeros_like(d)
+        hitq = -1 * m.ones_like(tg)
+        for q in range(len(self.qc)):
+            e1, e2, c = X.arr(self.qe1[q]), X.arr(self.qe2[q]), X.arr(self.qc[q])
+            nq = X.cross(e1[None], e2[None])[0]
+            tq = ((c - o) @ nq) / (d @ nq)
+            p = o + tq[..., None] * d - c
+            a = (p @ e1) / (e1 @ e1)
+            b = (p @ e2) / (e2 @ e2)
+            hit = (tq > 1e-3) & (tq < tmin) & (m.abs(a) <= 1) & (m.abs(b) <= 1)
+            tmin = m.where(hit, tq, tmin)
+            hitq = m.where(hit, q + 0.0 * tq, hitq)
+            nn = nq / X.norm(nq[None])[0]
+            flip = m.where((d @ nn) > 0, -1.0 + 0.0 * tq, 1.0 + 0.0 * tq)
+            n = m.where(hit[..., None], nn * flip[..., None], n)
+        fin = m.isfinite(tmin)
+        P = o + m.where(fin, tmin, 1e3 + 0.0 * tmin)[..., None] * d
+        on_ground = (hitq < 0) & fin
+        hx, hy = self._slopes(X, P[..., 0], P[..., 1])
+        ng = m.stack([-hx, -hy, m.ones_like(hx)], -1)
+        ng = ng / X.norm(ng)
+        n = m.where(on_ground[..., None], ng, n)
+        n = m.where((~fin)[..., None], -d, n)               # no surface: a far wall facing the camera
+        depth = m.where(fin, tmin, 1e3 + 0.0 * tmin)
+        cell = X.i64(m.floor(P[..., :2] / 0.25))
+        h = (cell[..., 0] * 73856093) ^ (cell[..., 1] * 19349663) ^ (X.i64(hitq) + 7) * 83492791 ^ self.rough_seed
+        rough = self.rough_lo + (1.0 - self.rough_lo) * ((h & 0xFFFF) / 65535.0)
+        return P, n, depth, rough
+
+    def _slopes(self, X, x, y):
+        hx, hy = 0.0 * x, 0.0 * x
+        for a, kx, ky, ph in self.hf.terms:
+            c = a * X.m.cos(kx * x + ky * y + ph)
+            hx = hx + c * kx
+            hy = hy + c * ky
+        return hx, hy
+
+    def _project(self, X, cam, P):
+        o, f, r, u = (X.arr(v) for v in (cam.origin, cam.fwd, cam.right, cam.up))
+        v = P - o
+        cz = v @ f
+        sx, sy = (v @ r) / cz, (v @ u) / cz
+        px = (sx / (self.tan_v * self.W / self.H) + 1) / 2 * self.W
+        py = (1 - sy / self.tan_v) / 2 * self.H
+        return px, py, cz
+
+    def _gbuffer(self, X, t):
+        m = X.m
+        P, n, depth, rough = self._cast(X, t)
+        g0 = X.f32(X.cat([n, depth[..., None]])).reshape(-1, 4)
+        px, py, cz = self._project(X, self.camera(t - 1), P)
+        xs, ys = X.meshgrid(X.arange(self.W) + 0.5, X.arange(self.H) + 0.5)
+        mvx = m.where(cz > 0, px - xs, 1e6 + 0.0 * px)
+        mvy = m.where(cz > 0, py - ys, 1e6 + 0.0 * py)
+        g1 = X.f32(m.stack([mvx, mvy, rough, 0.8 + 0.0 * rough], -1)).reshape(-1, 4)
+        if t == 0:
+            return g0, g1, g0
+        _, n_p, d_p, _ = self._cast(X, t - 1)
+        g0p = X.f32(X.cat([n_p, d_p[..., None]])).reshape(-1, 4)
+        return g0, g1, g0p
+
+    def gbuffer(self, t):
+        """(g0, g1, g0_prev) of frame t as float32 numpy arrays."""
+        return tuple(np.ascontiguousarray(a) for a in self._gbuffer(_NP(), t))
+
+    def gbuffer_on(self, t, device):
+        """(g0, g1, g0_prev) of frame t as contiguous float32 tensors on device."""
+        return tuple(a.contiguous() for a in self._gbuffer(_TORCH(device), t))
+
+
+def eight_lobe_field(seed):
+    return masked_lobe_field(seed, n_lobes=8, kappa_lo=5.0, kappa_hi=500.0, constant=0.02)
+
+
+def workload_4k(width=3840, height=2160, spp=4, frames=120):
+    """3840x2160, 4 spp, 120 frames: camera yawing 0.5 deg/frame over a
+    normal-mapped ground with 16 random occluding quads (depth discontinuities
+    and disocclusions that the depth test rejects); GGX roughness U(0.02, 1)
+    everywhere; radiance = 8 vMF lobes x occlusion mask + 0.02. FP16 Gamma, an
+    EM step followed by one gradient-refinement step per frame."""
+    seed = SEED_BASE + 5
+    sc = QuadScene(width, height, seed)
+    return dict(params=Params(width, height, spp=spp, seed=seed), camera=sc.camera, field=eight_lobe_field(seed),
+                frames=frames, gbuf=sc.gbuffer, scene=sc)
