@@ -38,6 +38,7 @@ struct Params {
     // analytic radiance field
     int n_lobes, mask_kind;
     float lobe_dir[8][3], lobe_kappa[8], lobe_scale[8];  // scale = amp * vMF normaliser
+    float lobe_e2[8];                                     // -kappa log2(e) / 2: exponent per |w - d|^2 in base 2
     float field_const, mask[3];
     // Gauss-Legendre rules on [-1, 1] with 4, 6 and 8 nodes, back to back
     // (computed on the host at context creation)
@@ -71,6 +72,14 @@ __device__ __forceinline__ float unit24_open0(uint32_t w) {
 // far from the overflow of 1/y, a correctly rounded division otherwise (the
 // latter's slow path is then taken only for extreme operands).
 __device__ __forceinline__ float fdiv(float x, float y) { return y > 1e-30f ? __fdividef(x, y) : __fdiv_rn(x, y); }
+
+// 2^x by the hardware approximation (relative error below 2^-22 over the
+// normal range; results below the smallest normal flush to zero).
+__device__ __forceinline__ float exp2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // sin and cos of 2 pi x for x in [0, 1): shifted by half a turn into [-pi, pi),
 // where the hardware approximation holds its 2^-21.4 absolute accuracy.
@@ -369,8 +378,9 @@ __device__ __forceinline__ float normal_tail(float h) {
 // so Z = (Phi(h1)-Phi(h0)) (Phi(k1)-Phi(k0)) + signed sum of the four corner
 // integrals, each by a Gauss-Legendre rule in t of 4, 6 or 8 nodes chosen by
 // |rho| (abs. error ~1e-8 up to |rho| = 0.9). As (h^2+k^2-2hks)/cos^2 t >=
-// max(h^2, k^2), a corner with max(h^2, k^2) > 50 contributes below e^-25
-// and is skipped.
+// max(h^2, k^2), and >= h^2 + k^2 when hk rho <= 0, a corner whose bound
+// exceeds 36 contributes below e^-18 (times asin(rho)/(2 pi) < 0.18) and is
+// skipped.
 __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, float isx, float isy, float rho) {
     const float h0 = -mx * isx, h1 = (1.0f - mx) * isx;
     const float k0 = -my * isy, k1 = (1.0f - my) * isy;
@@ -378,22 +388,34 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
     const float dpy = 1.0f - normal_tail(-k0) - normal_tail(k1);
     float z = dpx * dpy;
     const float h0s = h0 * h0, h1s = h1 * h1, k0s = k0 * k0, k1s = k1 * k1;
-    const bool c00 = fmaxf(h0s, k0s) <= 50.0f, c10 = fmaxf(h1s, k0s) <= 50.0f;
-    const bool c01 = fmaxf(h0s, k1s) <= 50.0f, c11 = fmaxf(h1s, k1s) <= 50.0f;
+    // a corner contributes below e^-18 when its exponent bound exceeds 18:
+    // (h^2 + k^2)/2 if h k rho <= 0 (the cross term only adds), else max(h^2, k^2)/2
+    auto live = [&](float h, float k, float hs, float ks) {
+        const float bound = (h * k * rho <= 0.0f) ? hs + ks : fmaxf(hs, ks);
+        return bound <= 36.0f;
+    };
+    const bool c00 = live(h0, k0, h0s, k0s), c10 = live(h1, k0, h1s, k0s);
+    const bool c01 = live(h0, k1, h0s, k1s), c11 = live(h1, k1, h1s, k1s);
     if (rho != 0.0f && (c00 || c10 || c01 || c11)) {
         const float ar = fabsf(rho);
         const int first = ar <= 0.6f ? 0 : (ar <= 0.75f ? 4 : 10);
         const int last = ar <= 0.6f ? 4 : (ar <= 0.75f ? 10 : kGLTotal);
         const float asr = asinf(rho), half = 0.5f * asr;
+        // exponent of corner (h, k) in base 2: (2hk s - h^2 - k^2) log2(e) / (2 cos^2 t)
+        const float l2 = 0.72134752044448170f;                  // log2(e) / 2
+        const float a00 = (h0s + k0s) * l2, b00 = 2.0f * h0 * k0 * l2;
+        const float a11 = (h1s + k1s) * l2, b11 = 2.0f * h1 * k1 * l2;
+        const float a10 = (h1s + k0s) * l2, b10 = 2.0f * h1 * k0 * l2;
+        const float a01 = (h0s + k1s) * l2, b01 = 2.0f * h0 * k1 * l2;
         float acc = 0.0f;
         for (int i = first; i < last; ++i) {
             const float s = sin_small(fmaf(half, P.gl_x[i], half));
-            const float ic = __fdividef(-0.5f, fmaf(-s, s, 1.0f));      // -1 / (2 cos^2 t), cos^2 t >= 0.19
+            const float q = __fdividef(1.0f, fmaf(-s, s, 1.0f));     // 1 / cos^2 t, cos^2 t >= 0.19
             float v = 0.0f;
-            if (c00) v += __expf((h0s + k0s - 2.0f * h0 * k0 * s) * ic);
-            if (c11) v += __expf((h1s + k1s - 2.0f * h1 * k1 * s) * ic);
-            if (c10) v -= __expf((h1s + k0s - 2.0f * h1 * k0 * s) * ic);
-            if (c01) v -= __expf((h0s + k1s - 2.0f * h0 * k1 * s) * ic);
+            if (c00) v += exp2_approx(fmaf(b00, s, -a00) * q);
+            if (c11) v += exp2_approx(fmaf(b11, s, -a11) * q);
+            if (c10) v -= exp2_approx(fmaf(b10, s, -a10) * q);
+            if (c01) v -= exp2_approx(fmaf(b01, s, -a01) * q);
             acc = fmaf(P.gl_w[i], v, acc);
         }
         z = fmaf(acc, half * kInv2Pi, z);
@@ -529,9 +551,12 @@ __device__ __forceinline__ bool brdf_sample(const Surf& s, float x1, float x2, f
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float radiance(const Params& P, float3 pos, float3 w) {
     float s = 0.0f;
-    for (int j = 0; j < P.n_lobes; ++j) {
-        const float dx = w.x - P.lobe_dir[j][0], dy = w.y - P.lobe_dir[j][1], dz = w.z - P.lobe_dir[j][2];
-        s = fmaf(P.lobe_scale[j], __expf(-0.5f * P.lobe_kappa[j] * (dx * dx + dy * dy + dz * dz)), s);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < P.n_lobes) {
+            const float dx = w.x - P.lobe_dir[j][0], dy = w.y - P.lobe_dir[j][1], dz = w.z - P.lobe_dir[j][2];
+            s = fmaf(P.lobe_scale[j], exp2_approx(P.lobe_e2[j] * fmaf(dx, dx, fmaf(dy, dy, dz * dz))), s);
+        }
     }
     if (P.mask_kind == 1) {
         const float m = 0.5f + 0.5f * sinpif(2.0f * (P.mask[0] * pos.x + P.mask[2] * w.x)) *
@@ -667,16 +692,30 @@ struct Kahan {
         c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
+    // the first term of a sum is exact: no compensation to carry
+    __device__ __forceinline__ void set(float v) { s = v; }
 };
 
 struct Stats {
     Kahan a, b, s1x, s1y, s2xx, s2yy, s2xy;
+    bool empty = true;
     __device__ __forceinline__ void add_train(const Guide& d, const Gam& g, const Smp& o) {
         if (o.strat != ST_BRDF || !(o.pb > 0.0f)) return;
-        const float w = o.fcos / o.pb;
-        const float gam = o.pmix > 0.0f ? d.pi_eff * o.pg / o.pmix : 0.0f;
+        const float w = fdiv(o.fcos, o.pb);
+        const float gam = o.pmix > 0.0f ? fdiv(d.pi_eff * o.pg, o.pmix) : 0.0f;
         const float wg = w * gam;
         const float dx = o.ux - g.ex, dy = o.uy - g.ey;
+        if (empty) {
+            a.set(wg);
+            b.set(w);
+            s1x.set(wg * dx);
+            s1y.set(wg * dy);
+            s2xx.set(wg * dx * dx);
+            s2yy.set(wg * dy * dy);
+            s2xy.set(wg * dx * dy);
+            empty = false;
+            return;
+        }
         a.add(wg);
         b.add(w);
         s1x.add(wg * dx);

@@ -140,9 +140,11 @@ pg_status field_params(const pg_field* f, Params& P, std::string& why) {
             // normalised vMF on the sphere: kappa / (2 pi (1 - exp(-2 kappa)))
             P.lobe_kappa[j] = (float)kap;
             P.lobe_scale[j] = (float)((double)f->amp[j] * kap / (2.0 * M_PI * -std::expm1(-2.0 * kap)));
+            P.lobe_e2[j] = (float)(-0.5 * kap / std::log(2.0));
         } else {
             P.lobe_kappa[j] = 0.0f;
             P.lobe_scale[j] = 0.0f;
+            P.lobe_e2[j] = 0.0f;
         }
     }
     P.field_const = f->constant;

@@ -7,8 +7,9 @@ projected Adam step).
 * One frame from a seeded Gamma: GPU (pg_frame, pg_grad, pg_adam_step) against
   the oracle's composition (frame, second_moment, adam). Adam's first step is
   lr * g / (|g| + eps), so a gradient component near zero has an ill-posed
-  sign; pixels with a component below 1% of their largest are excluded, as are
-  pixels with a draw within 1e-5 of a decision threshold.
+  sign: the adjoint agrees with the oracle to ~1e-3 of a pixel's largest
+  component, so pixels with a nonzero component below 1e-4 of their largest
+  are excluded, as are pixels with a draw within 1e-5 of a decision threshold.
 * Eight FP16 frames on the GPU: finite, in bounds, the expected rejection rate.
 """
 import numpy as np
@@ -50,7 +51,7 @@ def test_quad_workload_frame_plus_gradient_step_matches_oracle():
     assert 0.01 < 1 - acc.mean() < 0.12
     amb = (s["margin"] < 1e-5).reshape(spp, -1).any(0) | (margin < 1e-5)
     gmax = np.abs(rgrad).max(1, keepdims=True)
-    small = ((np.abs(rgrad) < 1e-2 * gmax) & (np.abs(rgrad) > 0)).any(1)
+    small = ((np.abs(rgrad) < 1e-4 * gmax) & (np.abs(rgrad) > 0)).any(1)
     ok = ~amb & ~small
     assert ok.mean() > 0.5
     assert (got[ok, 6] == ref[ok, 6]).all()
