@@ -599,10 +599,11 @@ void or_reproject(const or_config *cfg, const float *g0, const float *g1, const 
 /*   p_mix(w) = pi N(u)/(2 pi) + (1 - pi Z) p_b(w),  u = M^-1(w_local),     */
 /* and the one-sample balance-heuristic MIS estimate is F = f / p_mix.      */
 /* Random numbers: Philox4x32-10, key = seed, counter = (pixel, frame,      */
-/* sample, stream). Word 0 of stream 0 picks the strategy; words 1 and 2    */
-/* drive either Box-Muller (guide) or the BRDF draw (they are independent   */
-/* of word 0, so still uniform given the choice); a guide draw that left    */
-/* the square takes its BRDF draw from words 0 and 1 of stream 1.           */
+/* sample, stream). The top 24 bits of word 0 pick the strategy; those of   */
+/* words 1 and 2 drive either Box-Muller (guide) or the BRDF draw (they are */
+/* independent of word 0, so still uniform given the choice); a guide draw  */
+/* that left the square takes its BRDF draw from word 3 and from the low    */
+/* bytes of words 0-2, bits the decision has not looked at.                 */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double g5[5], chol[3], Z, pi_eff;
@@ -663,9 +664,10 @@ static void eval_local(const or_field *fld, const pixel_ctx *p, const double wl[
     *pmix = p->pi_eff * *pg + (1.0 - p->pi_eff * p->Z) * *pb;
 }
 
-/* One direction drawn from the mixture of pixel p: Philox counter (pixel,
- * frame, sample, stream0) for the strategy and Box-Muller / BRDF words,
- * (.., stream0 + 1) for a fallback. Returns the strategy; writes the local
+/* One direction drawn from the mixture of pixel p from the four words of
+ * Philox at counter (pixel, frame, sample, stream0): word 0 picks the
+ * strategy, words 1-2 drive Box-Muller or the BRDF draw, and a fallback draws
+ * from word 3 and the low bytes of words 0-2. Returns the strategy; writes the local
  * direction, whether it is valid, the square point when the guide drew it,
  * and the distance of the draw's decisions to their thresholds. */
 static int draw_direction(const pixel_ctx *p, const uint32_t key[2], uint32_t pix, uint32_t frame,
@@ -673,7 +675,6 @@ static int draw_direction(const pixel_ctx *p, const uint32_t key[2], uint32_t pi
                           int *valid, double *margin)
 {
     uint32_t c0[4] = {pix, frame, s, stream0}, r0[4];
-    uint32_t c1[4] = {pix, frame, s, stream0 + 1u}, r1[4];
     float pi_dec = (float)p->pi_eff; /* the strategy decision is taken in binary32 */
     or_philox(c0, key, r0);
     double zeta = unif(r0[0]);
@@ -695,9 +696,12 @@ static int draw_direction(const pixel_ctx *p, const uint32_t key[2], uint32_t pi
             *have_u = 1;
         } else {
             strat = S_FALLBACK;
-            or_philox(c1, key, r1);
+            /* fresh uniforms from the bits the draw has not used: word 3, and
+             * the low bytes of words 0-2 (independent of their top 24 bits) */
+            uint32_t spare = (r0[0] & 0xFFu) | ((r0[1] & 0xFFu) << 8) | ((r0[2] & 0xFFu) << 16);
             double mb;
-            *valid = or_brdf_sample(p->rough, p->wo_l, unif(r1[0]), unif(r1[1]), wl, &mb);
+            *valid = or_brdf_sample(p->rough, p->wo_l, unif(r0[3]), (double)spare * (1.0 / 16777216.0), wl,
+                                    &mb);
             if (mb < *margin) *margin = mb;
         }
     } else {

@@ -27,6 +27,7 @@ enum { ST_BRDF = 0, ST_GUIDE = 1, ST_FALLBACK = 2, ST_INVALID = 4 };
 struct Params {
     int W, H, spp, k_max;
     uint32_t key0, key1;
+    uint32_t rk[20];     // Philox round keys: (key0 + r W0, key1 + r W1) for rounds r = 0..9
     float pi_min, pi_max, pi_reinit;
     float depth_tol, normal_tol, rough_min, sigma2_min, rho_max;
     float init_raw[5];   // E[X], E[Y], E[X^2], E[Y^2], E[XY] of a re-initialised guide
@@ -49,6 +50,11 @@ struct Params {
 // Philox4x32-10 (Salmon et al., SC'11), counter-based: ten rounds of two
 // 32x32->64 multiplies with the key bumped by the Weyl constants in between.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1) {
+    // one 32x32 -> 64 product per multiplier gives both halves
+    const uint64_t p0 = (uint64_t)c.x * 0xD2511F53u, p1 = (uint64_t)c.z * 0xCD9E8D57u;
+    return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+}
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -56,10 +62,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
-        const uint32_t lo0 = c.x * 0xD2511F53u, hi0 = __umulhi(c.x, 0xD2511F53u);
-        const uint32_t lo1 = c.z * 0xCD9E8D57u, hi1 = __umulhi(c.z, 0xCD9E8D57u);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        c = philox_round(c, k0, k1);
     }
+    return c;
+}
+// the same with the round keys precomputed on the host (Params::rk)
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const uint32_t* rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) c = philox_round(c, rk[2 * r], rk[2 * r + 1]);
     return c;
 }
 // top 24 bits -> [0, 1) and (0, 1]; both exact in binary32
@@ -607,15 +617,16 @@ __device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, con
     }
 }
 
-// Random numbers: word 0 of Philox stream `stream0` (0 for the pass, 2 for the
-// adjoint's draws) picks the strategy; words 1 and 2 drive Box-Muller for a
-// guide draw or the BRDF draw otherwise (independent of word 0, hence still
-// uniform given the choice); a guide draw that left the square takes its BRDF
-// draw from stream `stream0 + 1`.
+// Random numbers: one Philox call per sample, at counter (pixel, frame,
+// sample, stream0) with stream0 = 0 for the pass and 2 for the adjoint's
+// draws. The top 24 bits of word 0 pick the strategy; those of words 1 and 2
+// drive Box-Muller for a guide draw or the BRDF draw otherwise (independent
+// of word 0, hence still uniform given the choice); a guide draw that left
+// the square takes its BRDF draw from word 3 and the low bytes of words 0-2.
 __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, const Surf& s, uint32_t pix,
                                            uint32_t frame, uint32_t si, uint32_t stream0 = 0u) {
     Smp o;
-    const uint4 r0 = philox4x32_10(make_uint4(pix, frame, si, stream0), P.key0, P.key1);
+    const uint4 r0 = philox4x32_10(make_uint4(pix, frame, si, stream0), P.rk);
     const float zeta = unit24(r0.x);
     bool have_u = false, valid;
     if (zeta < d.pi_eff) {
@@ -633,8 +644,10 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
             have_u = true;
         } else {
             o.strat = ST_FALLBACK;
-            const uint4 r1 = philox4x32_10(make_uint4(pix, frame, si, stream0 + 1u), P.key0, P.key1);
-            valid = brdf_sample(s, unit24(r1.x), unit24(r1.y), o.wl);
+            // fresh uniforms from bits the draw has not used: word 3 and the
+            // low bytes of words 0-2 (independent of their top 24 bits)
+            const uint32_t spare = (r0.x & 0xFFu) | ((r0.y & 0xFFu) << 8) | ((r0.z & 0xFFu) << 16);
+            valid = brdf_sample(s, unit24(r0.w), (float)spare * 5.9604644775390625e-8f, o.wl);
         }
     } else {
         o.strat = ST_BRDF;

@@ -55,11 +55,13 @@ __device__ __forceinline__ bool reproject_pixel(const Params& P, int x, int y, f
     return false;
 }
 
-template <int DT>
+// ONE: one sample per pixel, known at compile time (no sample loop, no Kahan
+// compensation state).
+template <int DT, bool ONE>
 __global__ void __launch_bounds__(kBlock, 4) k_frame(const Params P, const void* __restrict__ gin,
-                                                  void* __restrict__ gout, const float4* __restrict__ g0,
-                                                  const float4* __restrict__ g1, const float4* __restrict__ g0p,
-                                                  float* __restrict__ img, uint32_t frame, int* __restrict__ err) {
+                                                     void* __restrict__ gout, const float4* __restrict__ g0,
+                                                     const float4* __restrict__ g1, const float4* __restrict__ g0p,
+                                                     float* __restrict__ img, uint32_t frame, int* __restrict__ err) {
     const size_t hw = (size_t)P.W * P.H;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if ((size_t)i >= hw) return;
@@ -71,15 +73,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_frame(const Params P, const void*
     const Guide d = derive_guide(P, g, gated(P, reinit, a1));
     Stats st;
     Kahan f;
-    for (int si = 0; si < P.spp; ++si) {
+    const int spp = ONE ? 1 : P.spp;
+    for (int si = 0; si < spp; ++si) {
         const Smp o = draw_sample(P, d, s, (uint32_t)i, frame, (uint32_t)si);
-        f.add(o.F);
+        if (si == 0) f.set(o.F); else f.add(o.F);
         st.add_train(d, g, o);
     }
     m_step(P, g, st);
     if (!gam_finite(g)) atomicOr(err, 1);
     Store<DT>::store(gout, hw, (size_t)i, g);
-    if (img) __stcs(img + i, fdiv(f.s, (float)P.spp));
+    if (img) __stcs(img + i, ONE ? f.s : fdiv(f.s, (float)spp));
 }
 
 template <int DT>
@@ -405,7 +408,11 @@ cudaError_t launch_init(int dt, const Params& P, void* gam, float init_pi, cudaS
 cudaError_t launch_frame(int dt, const Params& P, const void* gin, void* gout, const float4* g0,
                          const float4* g1, const float4* g0p, float* img, uint32_t frame, int* err,
                          cudaStream_t st) {
-    PG_DISPATCH(dt, (k_frame<D><<<grid_for(P), kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
+    if (P.spp == 1) {
+        PG_DISPATCH(dt, (k_frame<D, true><<<grid_for(P), kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
+    } else {
+        PG_DISPATCH(dt, (k_frame<D, false><<<grid_for(P), kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
+    }
     return cudaGetLastError();
 }
 

@@ -87,6 +87,10 @@ void config_params(const pg_config& cfg, Params& P) {
     P.k_max = cfg.k_max;
     P.key0 = (uint32_t)(cfg.seed & 0xffffffffu);
     P.key1 = (uint32_t)(cfg.seed >> 32);
+    for (int r = 0; r < 10; ++r) {          // Philox4x32-10 round keys (Weyl increments)
+        P.rk[2 * r] = P.key0 + (uint32_t)r * 0x9E3779B9u;
+        P.rk[2 * r + 1] = P.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     P.pi_min = cfg.pi_min;
     P.pi_max = cfg.pi_max;
     P.pi_reinit = cfg.pi_reinit;
