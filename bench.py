@@ -137,13 +137,23 @@ def barrier(ws):
 
 
 def allmax(ws, v):
+    """v's maximum over the ranks (the slowest rank's time)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(ws, seconds, units_per_rank):
+    """Whole-job throughput under weak scaling: every rank processes its own
+    units_per_rank, so the job's rate is ws * units_per_rank over the slowest
+    rank's time. Returns (rate per second, slowest time in seconds)."""
+    tot = allmax(ws, seconds)
+    return ws * units_per_rank / tot, tot
 
 
 # ----------------------------------------------------------------------------
@@ -266,12 +276,12 @@ def reference_images(par, sc, fld, g0d, g1d, frames):
     return out
 
 
-def run_e2e(par, sc, fld, g0h, g1h, gamma_dtype, warmup, steps):
+def run_e2e(par, sc, fld, g0h, g1h, gamma_dtype, warmup, steps, seed_offset):
     """The same frames through the public API from pinned host buffers: every
     step copies its G-buffer host->device, runs the pass and reads the image
     back, all inside the timed region."""
     import torch
-    gp = make_pass(par, gamma_dtype)
+    gp = make_pass(par, gamma_dtype, seed_offset)
     hw = par.width * par.height
     g0d = [torch.empty((hw, 4), device="cuda") for _ in range(2)]
     g1d = torch.empty((hw, 4), device="cuda")
@@ -382,7 +392,7 @@ def run_gpu(args, ws, rank, local):
                "fp16": m["f16"], "ratio_fp16_over_fp32": m["f16"] / m["f32"],
                "matched": bool(m["f16"] <= 1.02 * m["f32"])}
 
-    e2e_ms, h2d, d2h = run_e2e(par, sc, fld, g0h, g1h, "f16", args.warmup, args.steps)
+    e2e_ms, h2d, d2h = run_e2e(par, sc, fld, g0h, g1h, "f16", args.warmup, args.steps, rank)
     del g0h, g1h, g0d, g1d
     w4k = None
     if not args.no_4k:
@@ -392,11 +402,10 @@ def run_gpu(args, ws, rank, local):
     res = {}
     for dt in ("f32", "f16"):
         ms = forms[dt][0]
-        tot = allmax(ws, sum(ms) / 1e3)
-        res[dt] = {"mpix_s": ws * hw * len(ms) / tot / 1e6, "ms_per_step": 1e3 * tot / len(ms),
-                   "gbs": BYTES_PER_PIXEL[dt] * hw * len(ms) / tot / 1e9 / ws}
-    e2e_tot = allmax(ws, sum(e2e_ms) / 1e3)
-    e2e_v = ws * hw * len(e2e_ms) / e2e_tot / 1e6
+        rate, tot = job_rate(ws, sum(ms) / 1e3, hw * len(ms))
+        res[dt] = {"mpix_s": rate / 1e6, "ms_per_step": 1e3 * tot / len(ms),
+                   "gbs": BYTES_PER_PIXEL[dt] * rate / ws / 1e9}
+    e2e_v = job_rate(ws, sum(e2e_ms) / 1e3, hw * len(e2e_ms))[0] / 1e6
     if rank != 0:
         return
     peak, peak_kind = measured_hbm()
