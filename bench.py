@@ -340,16 +340,88 @@ def run_4k(par, fld, sc, warmup, steps, flush):
     torch.cuda.synchronize()
     gp.pg_check()
     gp.close()
+    # rejection rate of the timed frames, from the staged reprojection's accept mask
+    acc = torch.empty(hw, dtype=torch.uint8, device="cuda")
+    rej = []
+    for t in range(warmup, warmup + steps):
+        g0, g1, g0p = frames[t]
+        chk = GuidePass(par.width, par.height, spp=par.spp, gamma_dtype="f16", seed=par.seed)
+        chk.pg_reproject(g0, g1, sc.camera(t), g0p, acc)
+        rej.append(1.0 - float(acc.float().mean()))
+        chk.close()
     fm = [e[0].elapsed_time(e[1]) for e in t_frame]
     gm = [e[1].elapsed_time(e[2]) for e in t_frame]
     f, g = sum(fm) / len(fm), sum(gm) / len(gm)
     peak, _ = measured_hbm()
     return {"workload": "3840x2160, 4 spp, FP16 Gamma: camera orbiting 0.5 deg/frame over a normal-mapped ground "
-                        "with 16 occluding quads (~5% reprojection rejections), GGX U(0.02,1), 8 vMF lobes x mask",
+                        "with 16 occluding quads, GGX U(0.02,1), 8 vMF lobes x mask",
             "frames_timed": steps, "frame_ms": f, "grad_adam_ms": g,
             "frame_mpix_s": hw / f / 1e3, "step_mpix_s": hw / (f + g) / 1e3,
             "frame_hbm_frac": BYTES_PER_PIXEL["f16"] * hw / (f * 1e-3) / 1e9 / peak,
-            "kernels_per_frame": 3}
+            "rejection_rate": sum(rej) / len(rej), "kernels_per_frame": 3}
+
+
+def run_diff(width=512, height=512, spp=64, steps=20, lr=1e-2, eval_frames=4, ref_spp=256):
+    """Differentiation form against EM at equal samples: two FP32 guides start
+    from the same state; one takes `steps` EM steps (the fused pass at `spp`
+    samples per pixel), the other `steps` projected-Adam steps on the
+    second-moment loss (adjoint over `spp` fresh draws per pixel). Each guide
+    is then scored by the estimator's second moment E[F^2] over held-out draws
+    (eval_frames x spp per pixel) and its variance E[F^2] - I^2, with I per
+    pixel from a ref_spp-sample estimate. Steps are timed with CUDA events."""
+    import torch
+    from paper_2112_09728_gb300 import scenes
+    wl = scenes.workload_diff(width, height, spp, steps)
+    par, cam, fld = wl["params"], wl["camera"], wl["field"]
+    g0h, g1h, _ = wl["gbuf"](0)
+    g0, g1 = torch.from_numpy(g0h).cuda(), torch.from_numpy(g1h).cuda()
+    hw = width * height
+    loss = torch.empty(hw, device="cuda")
+    grad = torch.empty((6, hw), device="cuda")
+    img = torch.empty(hw, device="cuda")
+
+    ref = make_pass(par, "f32", seed_offset=977, spp=ref_spp)
+    ref.pg_reproject(g0, g1, cam, g0)
+    ref.pg_sample(g0, g1, cam, fld, 0, None, img)
+    i2 = img.double() ** 2
+    ref.close()
+
+    def score(gp):
+        m2 = torch.zeros(hw, dtype=torch.float64, device="cuda")
+        for j in range(eval_frames):
+            gp.pg_grad(g0, g1, cam, fld, 1000000 + j, spp, loss=loss, grad=grad)
+            m2 += loss.double()
+        m2 /= eval_frames
+        return {"second_moment": float(m2.mean()), "variance": float((m2 - i2).mean())}
+
+    em, ad = make_pass(par, "f32", spp=spp), make_pass(par, "f32", spp=spp)
+    initial = score(em)
+    ev_em, ev_ad = [], []
+    for t in range(steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        em.pg_frame(g0, g1, cam, g0, fld, t, img)
+        e[1].record()
+        ev_em.append(e)
+    for t in range(steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        ad.pg_grad(g0, g1, cam, fld, t, spp, loss=loss, grad=grad)
+        ad.pg_adam_step(grad, lr=lr, step=t + 1)
+        e[1].record()
+        ev_ad.append(e)
+    torch.cuda.synchronize()
+    em.pg_check()
+    ad.pg_check()
+    out = {"workload": "%dx%d, flat Lambertian 0.8, two vMF lobes + 0.05, FP32 Gamma from mu=(0.5,0.5), "
+                       "Sigma=0.1 I, pi=0.5; %d samples per pixel per step" % (width, height, spp),
+           "steps": steps, "adam_lr": lr, "held_out_samples_per_pixel": eval_frames * spp,
+           "initial": initial, "em": score(em), "adam": score(ad),
+           "em_ms_per_step": sum(a.elapsed_time(b) for a, b in ev_em) / steps,
+           "adam_ms_per_step": sum(a.elapsed_time(b) for a, b in ev_ad) / steps}
+    em.close()
+    ad.close()
+    return out
 
 
 def run_gpu(args, ws, rank, local):
@@ -398,6 +470,7 @@ def run_gpu(args, ws, rank, local):
     if not args.no_4k:
         wl4 = scenes.workload_4k()
         w4k = run_4k(wl4["params"], wl4["field"], wl4["scene"], 4, 8, flush)
+    diff = None if args.no_diff else run_diff()
 
     res = {}
     for dt in ("f32", "f16"):
@@ -434,6 +507,7 @@ def run_gpu(args, ws, rank, local):
         "e2e": {"value": e2e_v, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "GuidePass.pg_frame with pinned-host G-buffer copies and image read-back"},
         "workload_4k": w4k,
+        "diff_form": diff,
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
@@ -449,6 +523,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 EM + gradient-step leg")
+    ap.add_argument("--no-diff", action="store_true", help="skip the 512x512 Adam-versus-EM comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

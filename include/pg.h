@@ -196,7 +196,7 @@ pg_status pg_eval(pg_ctx *ctx, const pg_gbuffer *cur, const pg_field *field, int
  * variance objective beside the EM step of Sec. 3.2). With theta =
  * (mu_x, mu_y, s_xx, s_yy, s_xy, pi) the guide's regularised mean,
  * covariance and mixing weight, n_samples directions w_i are drawn from the
- * guide at theta (Philox streams 2 and 3 of `frame`) and the loss is the Monte
+ * guide at theta (Philox stream 2 of `frame`) and the loss is the Monte
  * Carlo second moment of the estimator, l = 1/n sum f_i^2 / p(w_i)^2; its
  * gradient with the draws held fixed is
  *   dl/dtheta = -1/n sum f_i^2 (dp/dtheta)(w_i) / p(w_i)^3,

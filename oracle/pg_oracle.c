@@ -934,7 +934,7 @@ void or_derive_pixels(const or_config *cfg, const or_camera *cam, const float *g
 /* Second-moment loss and its gradient: the differentiable form of the      */
 /* guide (not in the paper). theta = (mu_x, mu_y, s_xx, s_yy, s_xy, pi) of  */
 /* a pixel's guide, regularised as in the pass. n directions w_i are drawn  */
-/* from the guide at theta0 (Philox streams 2 and 3) and held fixed, so     */
+/* from the guide at theta0 (Philox stream 2) and held fixed, so           */
 /*   l(theta) = 1/n sum_i f_i^2 / (p_theta(w_i) p_theta0(w_i)),              */
 /* which at theta = theta0 is the Monte Carlo second moment of the          */
 /* estimator F = f / p, and                                                  */

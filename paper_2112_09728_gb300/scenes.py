@@ -107,6 +107,18 @@ def workload_small(width=64, height=64, spp=1, frames=8):
         gbuf=lambda t: (g0, g1, g0))
 
 
+def workload_diff(width=512, height=512, spp=64, steps=20):
+    """The 64x64 workload's scene (flat Lambertian 0.8, the same two lobes +
+    0.05) and initial guide on a 512x512 screen, 64 samples per pixel per
+    step: 20 gradient steps (projected Adam, lr 1e-2) on the second-moment
+    loss against 20 EM steps, each step on fresh samples."""
+    seed = SEED_BASE + 4
+    g0, g1 = flat_scene(width, height)
+    return dict(params=Params(width, height, spp=spp, seed=seed), camera=top_down_camera(
+        pixel_size=1.0 / width), field=two_lobe_field(SEED_BASE + 1), steps=steps,
+        gbuf=lambda t: (g0, g1, g0))
+
+
 # ----------------------------------------------------------------------------
 # Workload 2: 1920x1080 pan over a heightfield, mixed Lambertian / GGX.
 # ----------------------------------------------------------------------------

@@ -1,0 +1,61 @@
+"""Gradient refinement against EM at equal samples (the 512x512
+differentiation workload, at 16x16 here): the benchmark's comparison run
+on the GPU, against the same comparison composed from the oracle (EM
+frames; second-moment adjoint + projected Adam; held-out second moments).
+Both sides draw the same Philox numbers, so their scores agree up to
+binary32 rounding compounded over ten steps and the rare draw whose decision
+lies at a threshold: the scores (means over pixels) must agree to 5e-3
+relative. Both methods must also lower the estimator's second moment."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_09728_gb300 import scenes
+
+from _pg import ocam, ocfg, ofld
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _oracle_scores(W, spp, steps, lr, eval_frames):
+    wl = scenes.workload_diff(W, W, spp, steps)
+    par, cam, fld = wl["params"], wl["camera"], wl["field"]
+    g0, g1, _ = wl["gbuf"](0)
+    cfg, oc, of = ocfg(par), ocam(cam), ofld(fld)
+    hw = W * W
+
+    def score(g):
+        th = O.theta_from_gamma(cfg, g)
+        m2 = sum(O.second_moment(cfg, oc, of, 1000000 + j, spp, g0, g1, th)[0] for j in range(eval_frames))
+        return float((m2 / eval_frames).mean())
+
+    g_init = O.init_gamma(cfg, hw, pi=par.init_pi)
+    out = {"initial": score(g_init)}
+    g = g_init.copy()
+    for t in range(steps):
+        g = O.frame(cfg, oc, of, t, g0, g1, g0, g)[0]
+    out["em"] = score(g)
+    g, m, v = g_init.copy(), np.zeros((hw, 6)), np.zeros((hw, 6))
+    for t in range(steps):
+        grad = O.second_moment(cfg, oc, of, t, spp, g0, g1, O.theta_from_gamma(cfg, g))[1]
+        g, m, v = O.adam(cfg, g, grad, m, v, lr, 0.9, 0.999, 1e-8, t + 1)
+    out["adam"] = score(g)
+    return out
+
+
+def test_adam_versus_em_comparison_matches_oracle():
+    sys.path.insert(0, ROOT)
+    import bench
+    W, spp, steps, lr, ev = 16, 16, 10, 1e-2, 4
+    got = bench.run_diff(W, W, spp=spp, steps=steps, lr=lr, eval_frames=ev, ref_spp=64)
+    ref = _oracle_scores(W, spp, steps, lr, ev)
+    for k in ("initial", "em", "adam"):
+        assert abs(got[k]["second_moment"] - ref[k]) <= 5e-3 * ref[k], (k, got[k], ref[k])
+    assert got["em"]["second_moment"] < 0.9 * got["initial"]["second_moment"]
+    assert got["adam"]["second_moment"] < 0.9 * got["initial"]["second_moment"]
+    assert np.isfinite([got["em_ms_per_step"], got["adam_ms_per_step"]]).all()
