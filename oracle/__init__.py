@@ -45,7 +45,8 @@ class Config(C.Structure):
                 ("pi_min", C.c_double), ("pi_max", C.c_double), ("pi_reinit", C.c_double),
                 ("depth_tol", C.c_double), ("normal_tol", C.c_double),
                 ("rough_min", C.c_double), ("sigma2_min", C.c_double), ("rho_max", C.c_double),
-                ("init_mu", C.c_double * 2), ("init_sigma", C.c_double * 3)]
+                ("init_mu", C.c_double * 2), ("init_sigma", C.c_double * 3),
+                ("reuse_radius", C.c_int32)]
 
 
 class Camera(C.Structure):
@@ -97,6 +98,7 @@ def _load():
                 "or_second_moment": [_P, _P, _P, C.c_uint32, C.c_int, _P, _P, _P, _P, _P, _P, _P],
                 "or_adam": [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double,
                             C.c_double, C.c_double, C.c_double],
+                "or_reuse_picks": [_P, C.c_double, C.c_uint32, C.c_uint32, _P, _P, _P],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -108,6 +110,7 @@ def _load():
             lib.or_brdf_pdf.restype = C.c_double
             lib.or_brdf_sample.restype = C.c_int
             lib.or_radiance.restype = C.c_double
+            lib.or_reuse_picks.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -132,7 +135,7 @@ def _f32(a, shape=None):
 def make_config(width, height, spp=1, seed=0, k_max=32, pi_min=0.05, pi_max=0.95,
                 pi_reinit=0.05, depth_tol=0.1, normal_tol=0.9, rough_min=0.1,
                 sigma2_min=1e-4, rho_max=0.9, init_mu=(0.5, 0.5),
-                init_sigma=(0.1, 0.1, 0.0)) -> Config:
+                init_sigma=(0.1, 0.1, 0.0), reuse_radius=0) -> Config:
     """Thresholds that the GPU applies in binary32 are rounded to binary32 here
     so that both sides compare against the same number."""
     f32 = lambda v: float(np.float32(v))
@@ -144,6 +147,7 @@ def make_config(width, height, spp=1, seed=0, k_max=32, pi_min=0.05, pi_max=0.95
     c.rough_min, c.sigma2_min, c.rho_max = f32(rough_min), f32(sigma2_min), f32(rho_max)
     c.init_mu[:] = [f32(v) for v in init_mu]
     c.init_sigma[:] = [f32(v) for v in init_sigma]
+    c.reuse_radius = int(reuse_radius)
     return c
 
 
@@ -323,6 +327,16 @@ def update(cfg, cam, g0, g1, gam, samples, reinit=None):
     _load().or_update(C.byref(cfg), C.byref(cam), _ptr(g0), _ptr(g1), _ptr(out), _ptr(rein),
                       _ptr(wx), _ptr(wy), _ptr(wz), _ptr(rad), _ptr(strat))
     return out
+
+
+def reuse_picks(cfg, k, pix, frame_idx):
+    """Neighbour-VPL picks of one pixel: (dx, dy, sample) int arrays of length N."""
+    d = 2 * cfg.reuse_radius + 1
+    cmax = max((d * d - 1) * cfg.spp, 1)
+    dx, dy, sm = (np.zeros(cmax, np.int32) for _ in range(3))
+    n = _load().or_reuse_picks(C.byref(cfg), float(k), int(pix) & 0xFFFFFFFF, int(frame_idx) & 0xFFFFFFFF,
+                               _ptr(dx), _ptr(dy), _ptr(sm))
+    return dx[:n].copy(), dy[:n].copy(), sm[:n].copy()
 
 
 def frame(cfg, cam, field, frame_idx, g0, g1, g0_prev, gam_prev):

@@ -41,6 +41,7 @@ typedef struct {
     double pi_min, pi_max, pi_reinit;
     double depth_tol, normal_tol, rough_min, sigma2_min, rho_max;
     double init_mu[2], init_sigma[3];
+    int32_t reuse_radius;    /* neighbour-VPL reuse window radius R (0: off) */
 } or_config;
 
 typedef struct {
@@ -792,6 +793,9 @@ void or_sample(const or_config *cfg, const or_camera *cam, const or_field *fld, 
 /*   pi <- clamp(A / B, 0.05, 0.95), k <- min(k + 1, kMax), W <- B.         */
 /* A frame without BRDF-strategy energy (b = 0) leaves Gamma unchanged.     */
 /* ------------------------------------------------------------------------ */
+static void em_step(const or_config *cfg, double *gm, double a, double b, double s1x, double s1y,
+                    double s2xx, double s2yy, double s2xy);
+
 static void update_pixel(const or_config *cfg, const or_camera *cam, int x, int y,
                          const float *g0, const float *g1, double *gm, int reinit,
                          const double *wx, const double *wy, const double *wz,
@@ -821,6 +825,13 @@ static void update_pixel(const or_config *cfg, const or_camera *cam, int x, int 
         s1x += w * gam * u[0]; s1y += w * gam * u[1];
         s2xx += w * gam * u[0] * u[0]; s2yy += w * gam * u[1] * u[1]; s2xy += w * gam * u[0] * u[1];
     }
+    em_step(cfg, gm, a, b, s1x, s1y, s2xx, s2yy, s2xy);
+}
+
+/* The M-step of one pixel from its frame statistics (see above). */
+static void em_step(const or_config *cfg, double *gm, double a, double b, double s1x, double s1y,
+                    double s2xx, double s2yy, double s2xy)
+{
     double k = gm[G_K] < 0.0 ? 0.0 : gm[G_K];
     if (b > 0.0) {
         double kc = k < cfg->k_max ? k : cfg->k_max;
@@ -859,6 +870,127 @@ void or_update(const or_config *cfg, const or_camera *cam, const float *g0, cons
         }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Neighbour-VPL reuse (Sec. 3.2: the VPLs of nearby pixels also train a    */
+/* pixel's guide, which speeds up convergence without bias; Sec. 4.2: N     */
+/* close VPLs per pixel, N = (1 - k/kMax) 15 + 5).                          */
+/*                                                                          */
+/* Readings (the paper gives no more than the above):                       */
+/* - A VPL is one sample of the sampling step: its world direction w, the   */
+/*   radiance L it brought back and, for a BRDF-strategy draw, the density  */
+/*   p_src(w) with which its own pixel's BRDF drew it. The radiance field   */
+/*   is distant, so a VPL reused at pixel p keeps its direction and its L.  */
+/* - Candidates: the samples of the pixels of the (2R+1)^2 window around p, */
+/*   p excluded, C = ((2R+1)^2 - 1) spp of them, enumerated row by row      */
+/*   (dy, then dx, from -R), each pixel's samples consecutively.            */
+/* - N = 5 + floor(15 (kMax - k) / kMax) for the reprojected epoch count k  */
+/*   (clamped to [0, kMax]; a re-initialised pixel has k = 0), at most C.   */
+/* - The N picks are distinct: candidate (start + j stride) mod C for       */
+/*   j < N, start = floor(r C / 2^32) for word 0 r of Philox at counter     */
+/*   (pixel, frame, 0, 4), stride the smallest integer >= 0.618 C coprime   */
+/*   with C. Picks outside the image are dropped.                           */
+/* - Only BRDF-strategy VPLs train (the rule for the pixel's own samples,   */
+/*   Sec. 3.2). Each enters p's statistics with the importance weight       */
+/*   w = f_p(w) / p_src(w) (f_p = L f_r cos at p), the density that drew it  */
+/*   being its own pixel's BRDF: the sums stay unbiased estimates of the    */
+/*   integrals of f_p over the directions p_src covers. The posterior is    */
+/*   p's: gamma = pi N / p_mix at p. Own samples enter the same way.        */
+/* Pinned by: the pick law (count, distinctness, window, uniform offsets), */
+/* the exact statistics of a constant field over equal Lambertian pixels,  */
+/* and unbiasedness of the weights across tilted neighbours (statistical).  */
+/* ------------------------------------------------------------------------ */
+static int64_t gcd64(int64_t a, int64_t b) { while (b) { int64_t t = a % b; a = b; b = t; } return a; }
+
+static int64_t reuse_candidates(const or_config *cfg)
+{
+    int64_t d = 2 * (int64_t)cfg->reuse_radius + 1;
+    return (d * d - 1) * (int64_t)cfg->spp;
+}
+
+static int64_t reuse_stride(int64_t c)
+{
+    int64_t s = (618 * c + 999) / 1000;   /* ceil(0.618 c) */
+    if (s < 1) s = 1;
+    while (gcd64(s, c) != 1) ++s;
+    return s;
+}
+
+/* The picks of pixel pix in frame `frame` for reprojected epoch count k:
+ * window offsets and sample index of each; returns their number N. */
+int or_reuse_picks(const or_config *cfg, double k, uint32_t pix, uint32_t frame, int32_t *dx,
+                   int32_t *dy, int32_t *sample)
+{
+    if (cfg->reuse_radius <= 0) return 0;
+    int64_t c = reuse_candidates(cfg), stride = reuse_stride(c);
+    int64_t kc = k < 0.0 ? 0 : (k > cfg->k_max ? cfg->k_max : (int64_t)k);
+    int64_t n = 5 + (15 * (cfg->k_max - kc)) / cfg->k_max;
+    if (n > c) n = c;
+    uint32_t ctr[4] = {pix, frame, 0u, 4u}, key[2] = {cfg->seed_lo, cfg->seed_hi}, r[4];
+    or_philox(ctr, key, r);
+    int64_t start = (int64_t)(((uint64_t)r[0] * (uint64_t)c) >> 32);
+    int32_t d = 2 * cfg->reuse_radius + 1, center = (d * d - 1) / 2;
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t o = (start + j * stride) % c;
+        int32_t cell = (int32_t)(o / cfg->spp);
+        if (cell >= center) ++cell;   /* skip p itself */
+        dy[j] = cell / d - cfg->reuse_radius;
+        dx[j] = cell % d - cfg->reuse_radius;
+        sample[j] = (int32_t)(o % cfg->spp);
+    }
+    return (int)n;
+}
+
+/* Adds one VPL (world direction ww, radiance L, source BRDF density pb_src)
+ * to pixel p's statistics acc = {a, b, s1x, s1y, s2xx, s2yy, s2xy}. */
+static void vpl_stats(const pixel_ctx *p, const double ww[3], double L, double pb_src, double acc[7])
+{
+    double wl[3];
+    to_local(p->n, ww, wl);
+    if (wl[2] <= 0.0 || !(pb_src > 0.0)) return;
+    double u[2];
+    or_hemi_to_square(wl, u);
+    double fcos = L * or_brdf_cos(p->rough, p->albedo, p->wo_l, wl);
+    double pb = or_brdf_pdf(p->rough, p->wo_l, wl);
+    double pg = or_gauss_pdf(p->g5, u) / (2.0 * M_PI);
+    double pmix = p->pi_eff * pg + (1.0 - p->pi_eff * p->Z) * pb;
+    double w = fcos / pb_src;
+    double gam = pmix > 0.0 ? p->pi_eff * pg / pmix : 0.0;
+    acc[0] += w * gam; acc[1] += w;
+    acc[2] += w * gam * u[0]; acc[3] += w * gam * u[1];
+    acc[4] += w * gam * u[0] * u[0]; acc[5] += w * gam * u[1] * u[1]; acc[6] += w * gam * u[0] * u[1];
+}
+
+static void update_pixel_reuse(const or_config *cfg, const or_camera *cam, uint32_t frame, int x, int y,
+                               const float *g0, const float *g1, double *gm, int reinit,
+                               const or_samples *S)
+{
+    int W = cfg->width, H = cfg->height, spp = cfg->spp;
+    int64_t i = (int64_t)y * W + x, HW = (int64_t)W * H;
+    pixel_ctx p;
+    pixel_setup(cfg, cam, x, y, g0, g1, gm, reinit, &p);
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < spp; ++s) {
+        int64_t o = (int64_t)s * HW + i;
+        if (S->strategy[o] != S_BRDF) continue;
+        double ww[3] = {S->wx[o], S->wy[o], S->wz[o]};
+        vpl_stats(&p, ww, S->radiance[o], S->pb[o], acc);
+    }
+    int64_t cmax = reuse_candidates(cfg);
+    int32_t *dx = malloc(sizeof(int32_t) * 3 * (size_t)(cmax > 0 ? cmax : 1));
+    int32_t *dy = dx + cmax, *sm = dy + cmax;
+    int n = or_reuse_picks(cfg, gm[G_K], (uint32_t)i, frame, dx, dy, sm);
+    for (int j = 0; j < n; ++j) {
+        int qx = x + dx[j], qy = y + dy[j];
+        if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+        int64_t o = (int64_t)sm[j] * HW + (int64_t)qy * W + qx;
+        if (S->strategy[o] != S_BRDF) continue;
+        double ww[3] = {S->wx[o], S->wy[o], S->wz[o]};
+        vpl_stats(&p, ww, S->radiance[o], S->pb[o], acc);
+    }
+    free(dx);
+    em_step(cfg, gm, acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6]);
+}
+
 /* One whole frame: reprojection, sampling and training, pixel by pixel.
  * gam_prev and gam_out are HW x 8; samples S may have NULL planes except the
  * ones the training step reads (wx, wy, wz, radiance, strategy). */
@@ -867,17 +999,40 @@ void or_frame(const or_config *cfg, const or_camera *cam, const or_field *fld, u
               double *gam_out, uint8_t *accept, or_samples *S, double *img)
 {
     int W = cfg->width, H = cfg->height;
+    if (cfg->reuse_radius <= 0) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                int64_t i = (int64_t)y * W + x;
+                int32_t q;
+                int acc = reproject_pixel(cfg, x, y, g0, g1, g0p, gam_prev, gam_out + 8 * i, &q);
+                if (accept) accept[i] = (uint8_t)acc;
+                sample_pixel(cfg, cam, fld, frame, x, y, g0, g1, gam_out + 8 * i, !acc, S, img);
+                update_pixel(cfg, cam, x, y, g0, g1, gam_out + 8 * i, !acc, S->wx, S->wy, S->wz,
+                             S->radiance, S->strategy);
+            }
+        return;
+    }
+    /* with reuse, training needs every pixel's samples of this frame: the
+     * paper's two passes (path tracing, then training), Fig. 2 */
+    int64_t HW = (int64_t)W * H;
+    uint8_t *acc_all = malloc((size_t)HW);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             int64_t i = (int64_t)y * W + x;
             int32_t q;
-            int acc = reproject_pixel(cfg, x, y, g0, g1, g0p, gam_prev, gam_out + 8 * i, &q);
-            if (accept) accept[i] = (uint8_t)acc;
-            sample_pixel(cfg, cam, fld, frame, x, y, g0, g1, gam_out + 8 * i, !acc, S, img);
-            update_pixel(cfg, cam, x, y, g0, g1, gam_out + 8 * i, !acc, S->wx, S->wy, S->wz,
-                         S->radiance, S->strategy);
+            acc_all[i] = (uint8_t)reproject_pixel(cfg, x, y, g0, g1, g0p, gam_prev, gam_out + 8 * i, &q);
+            sample_pixel(cfg, cam, fld, frame, x, y, g0, g1, gam_out + 8 * i, !acc_all[i], S, img);
         }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            update_pixel_reuse(cfg, cam, frame, x, y, g0, g1, gam_out + 8 * i, !acc_all[i], S);
+        }
+    if (accept) memcpy(accept, acc_all, (size_t)HW);
+    free(acc_all);
 }
 
 /* Evaluate the mixture at caller-given world directions: for each pixel and
