@@ -30,6 +30,12 @@ WORKLOAD = ("1920x1080, 1 spp, 60 frames: orthographic camera panning 2 px/frame
 BYTES_PER_PIXEL = {"f32": (32 + 16 + 16 + 16) + (32 + 4), "f16": (16 + 16 + 16 + 16) + (16 + 4),
                    "bf16": (16 + 16 + 16 + 16) + (16 + 4)}
 MSE_FRAMES = range(30, 60)
+REUSE_R = 2
+# with reuse the frame is two passes: path tracing reads Gamma(t-1) and the
+# G-buffer (64 B) and writes the image and one 20-byte VPL; training reads
+# Gamma(t-1), the G-buffer and the VPL (84 B; neighbours' VPLs come from
+# cache) and writes Gamma(t) (16 B)
+BYTES_PER_PIXEL["reuse"] = (64 + 4 + 20) + (64 + 20 + 16)
 REF_SPP = 256
 
 
@@ -224,17 +230,17 @@ def upload_frames(sc, n_frames, pin=False):
     return g0, g1
 
 
-def make_pass(par, gamma_dtype, seed_offset=0, spp=1):
+def make_pass(par, gamma_dtype, seed_offset=0, spp=1, reuse_radius=0):
     from paper_2112_09728_gb300.guide import GuidePass
     return GuidePass(par.width, par.height, spp=spp, gamma_dtype=gamma_dtype, seed=par.seed + seed_offset,
-                     init_pi=par.init_pi)
+                     init_pi=par.init_pi, reuse_radius=reuse_radius)
 
 
-def run_form(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush, keep_frames, seed_offset):
+def run_form(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush, keep_frames, seed_offset, reuse_radius=0):
     """Run frames 0..warmup+steps-1; time each of the last `steps` with CUDA events
     (L2 flushed before each). Returns (per-step ms list, {frame: image})."""
     import torch
-    gp = make_pass(par, gamma_dtype, seed_offset)
+    gp = make_pass(par, gamma_dtype, seed_offset, reuse_radius=reuse_radius)
     hw = par.width * par.height
     img = torch.empty(hw, dtype=torch.float32, device="cuda")
     kept = {}
@@ -448,13 +454,16 @@ def run_gpu(args, ws, rank, local):
             forms[dt] = (ms, kept)
     barrier(ws)
     clocks = clk.summary()
+    # neighbour-VPL reuse (two passes per frame), FP16 Gamma, window radius REUSE_R
+    forms["reuse"] = run_form(par, sc, fld, g0d, g1d, "f16", args.warmup, args.steps, flush, keep, rank,
+                              reuse_radius=REUSE_R)
 
     # matched MSE against a 256-spp reference of frames 30-59
     mse = None
     if keep:
         ref = reference_images(par, sc, fld, g0d, g1d, sorted(keep))
         m = {}
-        for dt in ("f32", "f16"):
+        for dt in ("f32", "f16", "reuse"):
             acc = 0.0
             for t in sorted(keep):
                 d = (forms[dt][1][t].double() - ref[t].double())
@@ -462,7 +471,7 @@ def run_gpu(args, ws, rank, local):
             m[dt] = acc / len(keep)
         mse = {"frames": [min(keep), max(keep)], "reference": "%d spp" % REF_SPP, "fp32": m["f32"],
                "fp16": m["f16"], "ratio_fp16_over_fp32": m["f16"] / m["f32"],
-               "matched": bool(m["f16"] <= 1.02 * m["f32"])}
+               "matched": bool(m["f16"] <= 1.02 * m["f32"]), "fp16_reuse": m["reuse"]}
 
     e2e_ms, h2d, d2h = run_e2e(par, sc, fld, g0h, g1h, "f16", args.warmup, args.steps, rank)
     del g0h, g1h, g0d, g1d
@@ -473,7 +482,7 @@ def run_gpu(args, ws, rank, local):
     diff = None if args.no_diff else run_diff()
 
     res = {}
-    for dt in ("f32", "f16"):
+    for dt in ("f32", "f16", "reuse"):
         ms = forms[dt][0]
         rate, tot = job_rate(ws, sum(ms) / 1e3, hw * len(ms))
         res[dt] = {"mpix_s": rate / 1e6, "ms_per_step": 1e3 * tot / len(ms),
@@ -498,6 +507,10 @@ def run_gpu(args, ws, rank, local):
         "fp32_plain": {"value": res["f32"]["mpix_s"], "ms_per_step": res["f32"]["ms_per_step"],
                        "roofline_frac": res["f32"]["gbs"] / peak},
         "mse": mse,
+        "reuse": {"radius": REUSE_R, "gamma_storage": "f16", "kernels_per_frame": 2,
+                  "value": res["reuse"]["mpix_s"], "ms_per_step": res["reuse"]["ms_per_step"],
+                  "hbm_frac": res["reuse"]["gbs"] / peak,
+                  "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL["reuse"]},
         "roofline": {"bound": "hbm", "achieved": main["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": main["gbs"] / peak, "peak_kind": peak_kind,
                      "kernel": "k_frame<f16> (fused guide pass)",

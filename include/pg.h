@@ -73,7 +73,11 @@ typedef enum { PG_F32 = 0, PG_F16 = 1, PG_BF16 = 2 } pg_dtype;
  *   k_max      [32]   cap of the epoch counter; the EM step is 1/(min(k,k_max)+2)
  * init_mu / init_sigma (xx, yy, xy) / init_pi give the Gamma that pg_create
  * writes to every pixel; a rejected pixel is re-initialised with the same
- * mean and covariance but pi = pi_reinit, k = 0, W = 0. */
+ * mean and covariance but pi = pi_reinit, k = 0, W = 0.
+ * reuse_radius [0] neighbour-VPL reuse (Sec. 3.2, 4.2), R in [0, 8]: with
+ * R > 0 each pixel also trains on N = 5 + floor(15 (k_max - k) / k_max)
+ * distinct BRDF-strategy samples of the (2R+1)^2 window around it (see
+ * pg_frame). 0 turns reuse off. */
 typedef struct {
     int32_t width, height;   /* screen size in pixels, each in [1, 32768] */
     int32_t spp;             /* samples per pixel per frame, in [1, 1024] */
@@ -83,6 +87,7 @@ typedef struct {
     float pi_min, pi_max, pi_reinit;
     float depth_tol, normal_tol, rough_min, sigma2_min, rho_max;
     float init_mu[2], init_sigma[3], init_pi;
+    int32_t reuse_radius;
 } pg_config;
 
 /* Camera of one frame: the primary ray of pixel (x, y). Orthographic (kind 0):
@@ -180,7 +185,20 @@ pg_status pg_update(pg_ctx *ctx, const pg_gbuffer *cur, const pg_samples *d_in);
 
 /* The whole frame, steps (a)-(c) fused in one kernel: reads Gamma(t-1), the
  * G-buffer and last frame's g0, writes Gamma(t) and d_img (per-pixel mean
- * estimate, nullable). Requires no staged frame in progress. */
+ * estimate, nullable). Requires no staged frame in progress.
+ * With reuse_radius R > 0 the frame runs as the paper's two passes (Fig. 2):
+ * the path-tracing pass writes one VPL per sample into a buffer the context
+ * owns (world direction, radiance, and the density of the pixel's BRDF draw
+ * for a BRDF-strategy sample); the training pass then trains each pixel on
+ * its own BRDF-strategy VPLs and on N picks of its window: N = 5 +
+ * floor(15 (k_max - k) / k_max) for the reprojected k (at most the window's
+ * ((2R+1)^2 - 1) spp candidates), the candidates (s + j t) mod C for
+ * j < N, s = floor(r C / 2^32) with r word 0 of Philox at counter (pixel,
+ * frame, 0, 4), t the smallest integer >= 0.618 C coprime with C; picks
+ * off the screen are dropped. A reused VPL weighs f / p_src (f = L f_r cos at
+ * this pixel, p_src the density of the draw at its own pixel). The staged
+ * calls and pg_frame_noalloc do not reuse: they return PG_ERR_ARG when
+ * reuse_radius > 0. */
 pg_status pg_frame(pg_ctx *ctx, const pg_gbuffer *cur, const float *d_g0_prev,
                    const pg_field *field, uint32_t frame, float *d_img);
 

@@ -23,6 +23,8 @@ struct pg_ctx {
     int* d_err = nullptr;     // device flag: non-finite Gamma stored
     float* adam_m = nullptr;  // Adam moments of theta, [6][H*W] each (allocated on first use)
     float* adam_v = nullptr;
+    float4* vpl = nullptr;    // neighbour reuse: one VPL per sample {world direction, radiance}
+    float* vpl_pb = nullptr;  //   and the density of its BRDF draw (0: does not train)
     pgk::Params base;         // configuration part of the launch parameters
     std::string err;
 };
@@ -125,6 +127,11 @@ pg_status pg_create(const pg_config* cfg, void* stream, pg_ctx** out) {
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&c->gam[b], c->gam_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(int));
+    if (e == cudaSuccess && cfg->reuse_radius > 0) {
+        const size_t n = hw * (size_t)cfg->spp;
+        e = cudaMalloc(&c->vpl, n * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc(&c->vpl_pb, n * sizeof(float));
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         pg_destroy(c);
@@ -150,6 +157,7 @@ pg_status pg_set_stream(pg_ctx* c, void* stream) {
 pg_status pg_reproject(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, uint8_t* d_accept) {
     if (!c) return PG_ERR_ARG;
     if (c->phase != 0) return fail(c, PG_ERR_STATE, "pg_reproject: a staged frame is already in progress");
+    if (c->cfg.reuse_radius > 0) return fail(c, PG_ERR_ARG, "pg_reproject: neighbour reuse runs in pg_frame only");
     pg_status s = check_gbuffer(c, cur);
     if (s != PG_OK) return s;
     if (!d_g0_prev || !aligned16(d_g0_prev)) return fail(c, PG_ERR_ARG, "d_g0_prev NULL or not 16-byte aligned");
@@ -215,9 +223,19 @@ pg_status pg_frame(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, con
         return fail(c, PG_ERR_ARG, "d_img overlaps Gamma");
     pgk::Params P = c->base;
     if ((s = fill_camera(c, cur->camera, P)) != PG_OK || (s = fill_field(c, field, P)) != PG_OK) return s;
-    cudaError_t e = pgk::launch_frame(c->cfg.gamma_dtype, P, c->gam[c->cur], c->gam[c->cur ^ 1],
-                                      (const float4*)cur->g0, (const float4*)cur->g1, (const float4*)d_g0_prev,
-                                      d_img, frame, c->d_err, c->stream);
+    const float4 *g0 = (const float4*)cur->g0, *g1 = (const float4*)cur->g1, *g0p = (const float4*)d_g0_prev;
+    cudaError_t e;
+    if (c->cfg.reuse_radius > 0) {
+        // the paper's two passes: path tracing writes the VPLs, training reads them
+        e = pgk::launch_pt(c->cfg.gamma_dtype, P, c->gam[c->cur], g0, g1, g0p, d_img, frame, c->vpl, c->vpl_pb,
+                           c->stream);
+        if (e == cudaSuccess)
+            e = pgk::launch_train(c->cfg.gamma_dtype, P, c->gam[c->cur], c->gam[c->cur ^ 1], g0, g1, g0p, frame,
+                                  c->vpl, c->vpl_pb, c->d_err, c->stream);
+    } else {
+        e = pgk::launch_frame(c->cfg.gamma_dtype, P, c->gam[c->cur], c->gam[c->cur ^ 1], g0, g1, g0p, d_img, frame,
+                              c->d_err, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "pg_frame");
     c->cur ^= 1;
     return PG_OK;
@@ -380,6 +398,8 @@ void pg_destroy(pg_ctx* c) {
     if (c->d_err) cudaFree(c->d_err);
     if (c->adam_m) cudaFree(c->adam_m);
     if (c->adam_v) cudaFree(c->adam_v);
+    if (c->vpl) cudaFree(c->vpl);
+    if (c->vpl_pb) cudaFree(c->vpl_pb);
     delete c;
 }
 

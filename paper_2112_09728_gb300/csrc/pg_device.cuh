@@ -44,6 +44,9 @@ struct Params {
     // Gauss-Legendre rules on [-1, 1] with 4, 6 and 8 nodes, back to back
     // (computed on the host at context creation)
     float gl_x[kGLTotal], gl_w[kGLTotal];
+    // neighbour-VPL reuse: window radius (0 = off), number of candidates
+    // ((2R+1)^2 - 1) spp, and the stride of the walk through them
+    int reuse_r, reuse_c, reuse_stride;
 };
 
 // ---------------------------------------------------------------------------
@@ -716,8 +719,28 @@ struct Stats {
         if (o.strat != ST_BRDF || !(o.pb > 0.0f)) return;
         const float w = fdiv(o.fcos, o.pb);
         const float gam = o.pmix > 0.0f ? fdiv(d.pi_eff * o.pg, o.pmix) : 0.0f;
+        add(g, w, gam, o.ux, o.uy);
+    }
+    // One reused VPL (Sec. 3.2): world direction ww and radiance L of a
+    // BRDF-strategy draw whose own pixel's BRDF drew it with density pb_src.
+    // It enters with the importance weight f / pb_src and this pixel's
+    // posterior, the own samples of the reuse path included.
+    __device__ __forceinline__ void add_vpl(const Guide& d, const Gam& g, const Surf& s, float3 ww, float L,
+                                            float pb_src) {
+        const float3 wl = to_local(s.f, ww);
+        if (!(wl.z > 0.0f) || !(pb_src > 0.0f)) return;
+        float fr, pb;
+        brdf_eval(s, wl, fr, pb);
+        const float2 u = hemi_to_square(wl);
+        const float pg = guide_pdf(d, u.x, u.y);
+        const float pmix = d.pi_eff * pg + (1.0f - d.pi_eff * d.Z) * pb;
+        const float w = fdiv(L * fr, pb_src);
+        const float gam = pmix > 0.0f ? fdiv(d.pi_eff * pg, pmix) : 0.0f;
+        add(g, w, gam, u.x, u.y);
+    }
+    __device__ __forceinline__ void add(const Gam& g, float w, float gam, float ux, float uy) {
         const float wg = w * gam;
-        const float dx = o.ux - g.ex, dy = o.uy - g.ey;
+        const float dx = ux - g.ex, dy = uy - g.ey;
         if (empty) {
             a.set(wg);
             b.set(w);

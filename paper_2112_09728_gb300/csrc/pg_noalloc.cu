@@ -65,6 +65,10 @@ extern "C" pg_status pg_frame_noalloc(const pg_config* cfg, const pg_gbuffer* cu
                                       void* stream) {
     std::string why;
     if (!cfg || pgk::check_config(cfg, why) != PG_OK) return PG_ERR_ARG;
+    if (cfg->reuse_radius > 0) {
+        std::fprintf(stderr, "pg_frame_noalloc: neighbour reuse needs the VPL buffer of a context (pg_frame)\n");
+        return PG_ERR_ARG;
+    }
     const size_t hw = (size_t)cfg->width * cfg->height;
     if (hw > kStaticMaxPixels) {
         std::fprintf(stderr, "pg_frame_noalloc: %d x %d = %zu pixels exceeds the fixed scratch of %zu pixels\n",

@@ -76,6 +76,8 @@ pg_status check_config(const pg_config* c, std::string& why) {
         why = "initial guide must have mu in [0,1]^2 and a positive definite covariance";
         return PG_ERR_ARG;
     }
+    if (c->reuse_radius < 0 || c->reuse_radius > 8) { why = "reuse_radius outside [0, 8]"; return PG_ERR_ARG; }
+    if (c->reuse_radius > 0 && c->k_max < 1) { why = "neighbour reuse needs k_max >= 1"; return PG_ERR_ARG; }
     return PG_OK;
 }
 
@@ -111,6 +113,19 @@ void config_params(const pg_config& cfg, Params& P) {
     gauss_legendre(4, P.gl_x, P.gl_w);
     gauss_legendre(6, P.gl_x + 4, P.gl_w + 4);
     gauss_legendre(8, P.gl_x + 10, P.gl_w + 10);
+    // neighbour reuse: C candidates, walked with the smallest stride >= 0.618 C
+    // that is coprime with C (so N <= C picks are distinct)
+    P.reuse_r = cfg.reuse_radius;
+    if (cfg.reuse_radius > 0) {
+        const int d = 2 * cfg.reuse_radius + 1;
+        const int64_t c = (int64_t)(d * d - 1) * cfg.spp;
+        int64_t t = (618 * c + 999) / 1000;
+        if (t < 1) t = 1;
+        auto gcd = [](int64_t a, int64_t b) { while (b) { const int64_t r = a % b; a = b; b = r; } return a; };
+        while (gcd(t, c) != 1) ++t;
+        P.reuse_c = (int)c;
+        P.reuse_stride = (int)t;
+    }
 }
 
 pg_status camera_params(const pg_camera& cam, Params& P, std::string& why) {

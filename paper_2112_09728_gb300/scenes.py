@@ -61,6 +61,7 @@ class Params:
     init_mu: tuple = (0.5, 0.5)
     init_sigma: tuple = (0.1, 0.1, 0.0)
     init_pi: float = 0.5
+    reuse_radius: int = 0      # neighbour-VPL reuse window radius (0: off)
 
 
 def unit_hemisphere_dirs(rng, n, zmin=0.0):
