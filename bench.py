@@ -283,34 +283,53 @@ def reference_images(par, sc, fld, g0d, g1d, frames):
 
 
 def run_e2e(par, sc, fld, g0h, g1h, gamma_dtype, warmup, steps, seed_offset):
-    """The same frames through the public API from pinned host buffers: every
-    step copies its G-buffer host->device, runs the pass and reads the image
-    back, all inside the timed region."""
+    """The same frames through the public API from pinned host buffers. Every
+    step uploads its G-buffer host->device, runs the pass (GuidePass.pg_frame)
+    and reads the image back device->host. The three run on their own streams,
+    so step t+1's upload and step t-1's read-back overlap step t's pass; rings
+    of device buffers (three g0, two g1, two images) are reused only after the
+    steps that read them have finished. The timed region spans the `steps`
+    timed steps from the first upload to the last read-back. Returns the per-step
+    share of that time and the bytes copied per step each way."""
     import torch
     gp = make_pass(par, gamma_dtype, seed_offset)
     hw = par.width * par.height
-    g0d = [torch.empty((hw, 4), device="cuda") for _ in range(2)]
-    g1d = torch.empty((hw, 4), device="cuda")
-    img = torch.empty(hw, device="cuda")
-    img_h = torch.empty(hw, pin_memory=True)
-    ms = []
-    for t in range(warmup + steps):
-        cur, prv = g0d[t % 2], g0d[(t - 1) % 2] if t > 0 else g0d[0]
-        timed = t >= warmup
-        if timed:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-        cur.copy_(g0h[t], non_blocking=True)
-        g1d.copy_(g1h[t], non_blocking=True)
-        gp.pg_frame(cur, g1d, sc.camera(t), prv if t > 0 else cur, fld, t, img)
-        img_h.copy_(img, non_blocking=True)
-        if timed:
-            e1.record()
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
+    n = warmup + steps
+    s_up, s_run, s_down = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    g0d = [torch.empty((hw, 4), device="cuda") for _ in range(3)]
+    g1d = [torch.empty((hw, 4), device="cuda") for _ in range(2)]
+    imgd = [torch.empty(hw, device="cuda") for _ in range(2)]
+    img_h = [torch.empty(hw, pin_memory=True) for _ in range(2)]
+    up, ran, down = ([torch.cuda.Event() for _ in range(n)] for _ in range(3))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for t in range(n):
+        if t == warmup:
+            torch.cuda.synchronize()
+            e0.record(s_up)
+        with torch.cuda.stream(s_up):
+            if t >= 2:
+                s_up.wait_event(ran[t - 2])      # g0d[t % 3] was step t-2's previous g0; g1d[t % 2] its g1
+            g0d[t % 3].copy_(g0h[t], non_blocking=True)
+            g1d[t % 2].copy_(g1h[t], non_blocking=True)
+            up[t].record(s_up)
+        with torch.cuda.stream(s_run):
+            s_run.wait_event(up[t])
+            if t >= 2:
+                s_run.wait_event(down[t - 2])    # imgd[t % 2] has been read back
+            prev = g0d[(t - 1) % 3] if t > 0 else g0d[0]
+            gp.pg_frame(g0d[t % 3], g1d[t % 2], sc.camera(t), prev, fld, t, imgd[t % 2])
+            ran[t].record(s_run)
+        with torch.cuda.stream(s_down):
+            s_down.wait_event(ran[t])
+            img_h[t % 2].copy_(imgd[t % 2], non_blocking=True)
+            down[t].record(s_down)
+    e1.record(s_down)
+    e1.synchronize()
+    total = e0.elapsed_time(e1)
     torch.cuda.synchronize()
     gp.close()
-    return ms, 2 * hw * 16, hw * 4
+    return [total / steps] * steps, 2 * hw * 16, hw * 4
 
 
 def run_4k(par, fld, sc, warmup, steps, flush):
@@ -365,6 +384,73 @@ def run_4k(par, fld, sc, warmup, steps, flush):
             "frame_mpix_s": hw / f / 1e3, "step_mpix_s": hw / (f + g) / 1e3,
             "frame_hbm_frac": BYTES_PER_PIXEL["f16"] * hw / (f * 1e-3) / 1e9 / peak,
             "rejection_rate": sum(rej) / len(rej), "kernels_per_frame": 3}
+
+
+def run_staged(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush):
+    """The staged frame (pg_reproject, pg_sample writing the per-sample
+    records, pg_update reading them back: the paper's path-tracing and
+    training passes with the VPL texture in memory) on the same frames as the
+    fused pass, each frame timed with CUDA events after an L2 flush."""
+    import torch
+    from paper_2112_09728_gb300.guide import alloc_samples
+    gp = make_pass(par, gamma_dtype)
+    hw = par.width * par.height
+    img = torch.empty(hw, device="cuda")
+    smp = alloc_samples(1, hw)
+    ms = []
+    for t in range(warmup + steps):
+        prev = max(t - 1, 0)
+        timed = t >= warmup
+        if timed:
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+        cam = sc.camera(t)
+        gp.pg_reproject(g0d[t], g1d[t], cam, g0d[prev])
+        gp.pg_sample(g0d[t], g1d[t], cam, fld, t, smp, img)
+        gp.pg_update(g0d[t], g1d[t], cam, smp)
+        if timed:
+            e1.record()
+            ms.append((e0, e1))
+    torch.cuda.synchronize()
+    gp.pg_check()
+    gp.close()
+    return [a.elapsed_time(b) for a, b in ms]
+
+
+def run_temporal(width=1920, height=1080, frames=60, tail=30):
+    """Temporal stability (the synthetic analogue of the paper's flicker plot,
+    Fig. 4, without a denoiser): a static camera, 1 spp, `frames` frames; the
+    mean squared difference between consecutive images over the last `tail`
+    frames, with the guide (FP16 Gamma) and with BRDF sampling alone (pi held
+    at 0)."""
+    import torch
+    from paper_2112_09728_gb300 import scenes
+    from paper_2112_09728_gb300.guide import GuidePass
+    wl = scenes.workload_static(width, height, frames=frames)
+    par, fld, sc = wl["params"], wl["field"], wl["scene"]
+    g0h, g1h, _ = sc.gbuffer(0)
+    g0, g1 = torch.from_numpy(g0h).cuda(), torch.from_numpy(g1h).cuda()
+    hw = width * height
+    out = {}
+    for name, kw in (("guided", dict(init_pi=par.init_pi)),
+                     ("brdf_only", dict(init_pi=0.0, pi_min=0.0, pi_max=0.0, pi_reinit=0.0))):
+        gp = GuidePass(width, height, gamma_dtype="f16", seed=par.seed, **kw)
+        prev, cur = torch.empty(hw, device="cuda"), torch.empty(hw, device="cuda")
+        acc, mean = 0.0, 0.0
+        for t in range(frames):
+            gp.pg_frame(g0, g1, sc.camera(t), g0, fld, t, cur)
+            if t >= frames - tail:
+                acc += float(((cur.double() - prev.double()) ** 2).mean())
+                mean += float(cur.double().mean())
+            prev, cur = cur, prev
+        gp.pg_check()
+        gp.close()
+        out[name] = {"temporal_mse": acc / tail, "mean_image": mean / tail}
+    out["ratio_guided_over_brdf_only"] = out["guided"]["temporal_mse"] / out["brdf_only"]["temporal_mse"]
+    out["workload"] = "%dx%d static camera, 1 spp, %d frames (last %d measured), heightfield materials and " \
+                      "masked 4-lobe field of the 1080p workload" % (width, height, frames, tail)
+    return out
 
 
 def run_diff(width=512, height=512, spp=64, steps=20, lr=1e-2, eval_frames=4, ref_spp=256):
@@ -457,6 +543,7 @@ def run_gpu(args, ws, rank, local):
     # neighbour-VPL reuse (two passes per frame), FP16 Gamma, window radius REUSE_R
     forms["reuse"] = run_form(par, sc, fld, g0d, g1d, "f16", args.warmup, args.steps, flush, keep, rank,
                               reuse_radius=REUSE_R)
+    staged_ms = run_staged(par, sc, fld, g0d, g1d, "f16", args.warmup, args.steps, flush)
 
     # matched MSE against a 256-spp reference of frames 30-59
     mse = None
@@ -480,6 +567,7 @@ def run_gpu(args, ws, rank, local):
         wl4 = scenes.workload_4k()
         w4k = run_4k(wl4["params"], wl4["field"], wl4["scene"], 4, 8, flush)
     diff = None if args.no_diff else run_diff()
+    temporal = None if args.no_temporal else run_temporal()
 
     res = {}
     for dt in ("f32", "f16", "reuse"):
@@ -507,6 +595,8 @@ def run_gpu(args, ws, rank, local):
         "fp32_plain": {"value": res["f32"]["mpix_s"], "ms_per_step": res["f32"]["ms_per_step"],
                        "roofline_frac": res["f32"]["gbs"] / peak},
         "mse": mse,
+        "staged": {"ms_per_step": sum(staged_ms) / len(staged_ms), "gamma_storage": "f16", "kernels_per_frame": 3,
+                   "fused_speedup": (sum(staged_ms) / len(staged_ms)) / res["f16"]["ms_per_step"]},
         "reuse": {"radius": REUSE_R, "gamma_storage": "f16", "kernels_per_frame": 2,
                   "value": res["reuse"]["mpix_s"], "ms_per_step": res["reuse"]["ms_per_step"],
                   "hbm_frac": res["reuse"]["gbs"] / peak,
@@ -518,9 +608,11 @@ def run_gpu(args, ws, rank, local):
                      "traffic_unit": "bytes per launch (ncu dram read+write, profiles/k_frame_1080p_pan.md)"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_v, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "api": "GuidePass.pg_frame with pinned-host G-buffer copies and image read-back"},
+                "api": "GuidePass.pg_frame with pinned-host G-buffer uploads and image read-backs, "
+                       "upload / pass / read-back on three streams (steps overlap)"},
         "workload_4k": w4k,
         "diff_form": diff,
+        "temporal_stability": temporal,
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
@@ -537,6 +629,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 EM + gradient-step leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the 512x512 Adam-versus-EM comparison")
+    ap.add_argument("--no-temporal", action="store_true", help="skip the static-camera temporal-stability leg")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -25,6 +25,7 @@ struct pg_ctx {
     float* adam_v = nullptr;
     float4* vpl = nullptr;    // neighbour reuse: one VPL per sample {world direction, radiance}
     float* vpl_pb = nullptr;  //   and the density of its BRDF draw (0: does not train)
+    float* zbuf = nullptr;    //   and each pixel's rectangle mass Z, from the path-tracing pass
     pgk::Params base;         // configuration part of the launch parameters
     std::string err;
 };
@@ -131,6 +132,7 @@ pg_status pg_create(const pg_config* cfg, void* stream, pg_ctx** out) {
         const size_t n = hw * (size_t)cfg->spp;
         e = cudaMalloc(&c->vpl, n * sizeof(float4));
         if (e == cudaSuccess) e = cudaMalloc(&c->vpl_pb, n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&c->zbuf, hw * sizeof(float));
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -228,10 +230,10 @@ pg_status pg_frame(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, con
     if (c->cfg.reuse_radius > 0) {
         // the paper's two passes: path tracing writes the VPLs, training reads them
         e = pgk::launch_pt(c->cfg.gamma_dtype, P, c->gam[c->cur], g0, g1, g0p, d_img, frame, c->vpl, c->vpl_pb,
-                           c->stream);
+                           c->zbuf, c->stream);
         if (e == cudaSuccess)
             e = pgk::launch_train(c->cfg.gamma_dtype, P, c->gam[c->cur], c->gam[c->cur ^ 1], g0, g1, g0p, frame,
-                                  c->vpl, c->vpl_pb, c->d_err, c->stream);
+                                  c->vpl, c->vpl_pb, c->zbuf, c->d_err, c->stream);
     } else {
         e = pgk::launch_frame(c->cfg.gamma_dtype, P, c->gam[c->cur], c->gam[c->cur ^ 1], g0, g1, g0p, d_img, frame,
                               c->d_err, c->stream);
@@ -400,6 +402,7 @@ void pg_destroy(pg_ctx* c) {
     if (c->adam_v) cudaFree(c->adam_v);
     if (c->vpl) cudaFree(c->vpl);
     if (c->vpl_pb) cudaFree(c->vpl_pb);
+    if (c->zbuf) cudaFree(c->zbuf);
     delete c;
 }
 

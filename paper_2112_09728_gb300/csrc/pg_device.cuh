@@ -47,6 +47,7 @@ struct Params {
     // neighbour-VPL reuse: window radius (0 = off), number of candidates
     // ((2R+1)^2 - 1) spp, and the stride of the walk through them
     int reuse_r, reuse_c, reuse_stride;
+    float reuse_inv_spp, reuse_inv_dw;   // 1/spp and 1/(2R+1), for exact floor divisions of small integers
 };
 
 // ---------------------------------------------------------------------------
@@ -436,7 +437,8 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
     return z;
 }
 
-__device__ __forceinline__ Guide derive_guide(const Params& P, const Gam& g, bool gated) {
+// Everything of the derived guide but Z (left at 1).
+__device__ __forceinline__ Guide derive_guide_shape(const Params& P, const Gam& g, bool gated) {
     Guide d;
     d.mx = fminf(fmaxf(g.ex, 0.0f), 1.0f);
     d.my = fminf(fmaxf(g.ey, 0.0f), 1.0f);
@@ -453,7 +455,16 @@ __device__ __forceinline__ Guide derive_guide(const Params& P, const Gam& g, boo
     d.l22 = c22 * d.il22;
     d.pnorm = kInv4Pi2 * d.il11 * d.il22;
     d.pi_eff = gated ? 0.0f : g.pi;
-    d.Z = (d.pi_eff > 0.0f) ? rect_mass(P, d.mx, d.my, d.il11, isy, d.sxy * d.il11 * isy) : 1.0f;
+    d.Z = 1.0f;
+    return d;
+}
+
+__device__ __forceinline__ Guide derive_guide(const Params& P, const Gam& g, bool gated) {
+    Guide d = derive_guide_shape(P, g, gated);
+    if (d.pi_eff > 0.0f) {
+        const float isy = rsqrtf(d.syy);
+        d.Z = rect_mass(P, d.mx, d.my, d.il11, isy, d.sxy * d.il11 * isy);
+    }
     return d;
 }
 

@@ -125,6 +125,8 @@ void config_params(const pg_config& cfg, Params& P) {
         while (gcd(t, c) != 1) ++t;
         P.reuse_c = (int)c;
         P.reuse_stride = (int)t;
+        P.reuse_inv_spp = 1.0f / (float)cfg.spp;
+        P.reuse_inv_dw = 1.0f / (float)d;
     }
 }
 

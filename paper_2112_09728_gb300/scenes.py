@@ -210,6 +210,17 @@ def workload_pan(width=1920, height=1080, spp=1, frames=60):
                 field=masked_lobe_field(seed), frames=frames, gbuf=sc.gbuffer, scene=sc)
 
 
+def workload_static(width=1920, height=1080, spp=1, frames=60):
+    """The 1080p workload's heightfield, materials and radiance field under a
+    static camera (zero motion vectors, the same G-buffer every frame): the
+    setting of the temporal-stability measurement, where the difference
+    between consecutive images is pure sampling noise."""
+    seed = SEED_BASE + 2
+    sc = PanScene(width, height, frames, seed, pan=0)
+    return dict(params=Params(width, height, spp=spp, seed=seed), camera=sc.camera,
+                field=masked_lobe_field(seed), frames=frames, gbuf=sc.gbuffer, scene=sc)
+
+
 # ----------------------------------------------------------------------------
 # Random guide states, directions and sample sets for unit parity.
 # ----------------------------------------------------------------------------
