@@ -418,6 +418,43 @@ def run_staged(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush):
     return [a.elapsed_time(b) for a, b in ms]
 
 
+def run_rounding(frames=300, k_max=256):
+    """Round-to-nearest against stochastic rounding of the 16-bit store where
+    EM steps get small: the 64x64 workload (every pixel sees the same
+    integrand) for `frames` frames with k_max = 256, so eta falls to 1/258.
+    Each form's guide, averaged over the pixels at the end, against the FP32
+    run's: rounding to nearest drops updates below half a storage ulp, so its
+    guide stalls; stochastic rounding keeps them in expectation."""
+    import torch
+    from paper_2112_09728_gb300 import scenes
+    from paper_2112_09728_gb300.guide import GuidePass, planes_to_rows
+    wl = scenes.workload_small(frames=frames)
+    par, cam, fld = wl["params"], wl["camera"], wl["field"]
+    g0h, g1h, _ = wl["gbuf"](0)
+    g0, g1 = torch.from_numpy(g0h).cuda(), torch.from_numpy(g1h).cuda()
+    out = {}
+    for name, dt, sr in (("f32", "f32", 0), ("f16_nearest", "f16", 0), ("f16_stochastic", "f16", 1),
+                         ("bf16_nearest", "bf16", 0), ("bf16_stochastic", "bf16", 1)):
+        gp = GuidePass(par.width, par.height, gamma_dtype=dt, seed=par.seed, init_pi=par.init_pi, k_max=k_max,
+                       stochastic_round=sr)
+        for t in range(frames):
+            gp.pg_frame(g0, g1, cam, g0, fld, t)
+        gp.pg_check()
+        r = planes_to_rows(gp.pg_gamma_to_f32()).double()
+        mx, my = r[:, 0], r[:, 1]
+        cen = torch.stack([mx, my, r[:, 2] - mx * mx, r[:, 3] - my * my, r[:, 4] - mx * my, r[:, 5], r[:, 7]], 1)
+        out[name] = cen.mean(0).tolist()
+        gp.close()
+    keys = ["mu_x", "mu_y", "s_xx", "s_yy", "s_xy", "pi", "W"]
+    ref = out["f32"]
+    rep = {"workload": "64x64 flat Lambertian, two lobes + 0.05, 1 spp, %d frames, k_max %d" % (frames, k_max),
+           "pixel_mean_f32": dict(zip(keys, ref))}
+    for name in out:
+        if name != "f32":
+            rep["abs_diff_vs_f32_" + name] = dict(zip(keys, [abs(a - b) for a, b in zip(out[name], ref)]))
+    return rep
+
+
 def run_temporal(width=1920, height=1080, frames=60, tail=30):
     """Temporal stability (the synthetic analogue of the paper's flicker plot,
     Fig. 4, without a denoiser): a static camera, 1 spp, `frames` frames; the
@@ -568,6 +605,7 @@ def run_gpu(args, ws, rank, local):
         w4k = run_4k(wl4["params"], wl4["field"], wl4["scene"], 4, 8, flush)
     diff = None if args.no_diff else run_diff()
     temporal = None if args.no_temporal else run_temporal()
+    rounding = None if args.no_temporal else run_rounding()
 
     res = {}
     for dt in ("f32", "f16", "reuse"):
@@ -613,6 +651,7 @@ def run_gpu(args, ws, rank, local):
         "workload_4k": w4k,
         "diff_form": diff,
         "temporal_stability": temporal,
+        "stochastic_rounding": rounding,
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
@@ -629,7 +668,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 EM + gradient-step leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the 512x512 Adam-versus-EM comparison")
-    ap.add_argument("--no-temporal", action="store_true", help="skip the static-camera temporal-stability leg")
+    ap.add_argument("--no-temporal", action="store_true",
+                    help="skip the static-camera temporal-stability and the stochastic-rounding legs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -77,7 +77,16 @@ typedef enum { PG_F32 = 0, PG_F16 = 1, PG_BF16 = 2 } pg_dtype;
  * reuse_radius [0] neighbour-VPL reuse (Sec. 3.2, 4.2), R in [0, 8]: with
  * R > 0 each pixel also trains on N = 5 + floor(15 (k_max - k) / k_max)
  * distinct BRDF-strategy samples of the (2R+1)^2 window around it (see
- * pg_frame). 0 turns reuse off. */
+ * pg_frame). 0 turns reuse off.
+ * stochastic_round [0] with FP16/BF16 storage, 1 rounds the Gamma written by
+ * an EM step stochastically instead of to nearest: each field goes to one of
+ * its two neighbours in the storage type with probability proportional to
+ * proximity (unbiased), using 16 bits of Philox at counter (pixel, frame, 0,
+ * 5) per field (field j: word j/2, bits 16 (j mod 2) and up). An update
+ * smaller than half a storage ulp then still moves the guide on average.
+ * pg_update takes `frame` from the pg_sample of its staged frame (0 without
+ * one). Values
+ * that are already representable are stored exactly either way. */
 typedef struct {
     int32_t width, height;   /* screen size in pixels, each in [1, 32768] */
     int32_t spp;             /* samples per pixel per frame, in [1, 1024] */
@@ -88,6 +97,7 @@ typedef struct {
     float depth_tol, normal_tol, rough_min, sigma2_min, rho_max;
     float init_mu[2], init_sigma[3], init_pi;
     int32_t reuse_radius;
+    int32_t stochastic_round;
 } pg_config;
 
 /* Camera of one frame: the primary ray of pixel (x, y). Orthographic (kind 0):

@@ -21,6 +21,7 @@ struct pg_ctx {
     float4* work = nullptr;   // binary32 work copy of the staged pass
     int phase = 0;            // 1 between pg_reproject and pg_update
     int* d_err = nullptr;     // device flag: non-finite Gamma stored
+    uint32_t sample_frame = 0;  // frame of the last pg_sample (rounding bits of pg_update)
     float* adam_m = nullptr;  // Adam moments of theta, [6][H*W] each (allocated on first use)
     float* adam_v = nullptr;
     float4* vpl = nullptr;    // neighbour reuse: one VPL per sample {world direction, radiance}
@@ -170,6 +171,7 @@ pg_status pg_reproject(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev,
                                           (const float4*)cur->g1, (const float4*)d_g0_prev, d_accept, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pg_reproject");
     c->phase = 1;
+    c->sample_frame = 0;
     return PG_OK;
 }
 
@@ -192,6 +194,7 @@ pg_status pg_sample(pg_ctx* c, const pg_gbuffer* cur, const pg_field* field, uin
     cudaError_t e = pgk::launch_sample(c->cfg.gamma_dtype, P, c->work, (const float4*)cur->g0, (const float4*)cur->g1,
                                        frame, o, d_img, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pg_sample");
+    c->sample_frame = frame;
     return PG_OK;
 }
 
@@ -204,6 +207,7 @@ pg_status pg_update(pg_ctx* c, const pg_gbuffer* cur, const pg_samples* d_in) {
         return fail(c, PG_ERR_ARG, "pg_update: wx, wy, wz, radiance and strategy are required");
     pgk::Params P = c->base;
     if ((s = fill_camera(c, cur->camera, P)) != PG_OK) return s;
+    P.sr_frame = c->sample_frame;
     pgk::SamplePlanes in{d_in->wx, d_in->wy, d_in->wz, d_in->radiance, nullptr, nullptr, nullptr, d_in->strategy};
     cudaError_t e = pgk::launch_update(c->cfg.gamma_dtype, P, c->work, (const float4*)cur->g0,
                                        (const float4*)cur->g1, in, c->gam[c->cur ^ 1], c->d_err, c->stream);

@@ -48,6 +48,8 @@ struct Params {
     // ((2R+1)^2 - 1) spp, and the stride of the walk through them
     int reuse_r, reuse_c, reuse_stride;
     float reuse_inv_spp, reuse_inv_dw;   // 1/spp and 1/(2R+1), for exact floor divisions of small integers
+    int sr;                              // stochastic rounding of the 16-bit EM stores
+    uint32_t sr_frame;                   // frame index of the staged update's rounding bits
 };
 
 // ---------------------------------------------------------------------------
@@ -243,6 +245,38 @@ __device__ __forceinline__ uint16_t HalfStore<__nv_bfloat16>::pack(float v) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
+// Stochastic rounding of a binary32 value to the storage type, from 16
+// random bits r: rounds to one of the two neighbours of v with probabilities
+// proportional to proximity, so the stored value is v in expectation (an EM
+// update below half a storage ulp still moves the guide on average).
+// FP16: |v| + u ulp16(|v|), u = (r >> 3) / 2^13, then toward zero; the sum is
+// exact in binary32 (u ulp16 is a multiple of binary32's ulp at |v|).
+// BF16: the random bits are added below bf16's last kept bit, then the low
+// half is dropped (a carry rounds the magnitude up).
+__device__ __forceinline__ uint16_t sr_pack_f16(float v, uint32_t r) {
+    if (!isfinite(v)) return __half_as_ushort(__float2half_rn(v));
+    const float a = fabsf(v);
+    const int e = max((int)(__float_as_uint(a) >> 23) - 127, -14);   // fp16 binade (subnormals: -14)
+    const float ulp = __uint_as_float((uint32_t)(e - 10 + 127) << 23);
+    const float b = __fmaf_rn((float)((r & 0xFFFFu) >> 3) * (1.0f / 8192.0f), ulp, a);
+    return __half_as_ushort(__float2half_rz(copysignf(b, v)));
+}
+__device__ __forceinline__ uint16_t sr_pack_bf16(float v, uint32_t r) {
+    if (!isfinite(v)) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    return (uint16_t)((__float_as_uint(v) + (r & 0xFFFFu)) >> 16);
+}
+
+template <typename H>
+struct SrPack;
+template <>
+struct SrPack<__half> {
+    static __device__ __forceinline__ uint16_t pack(float v, uint32_t r) { return sr_pack_f16(v, r); }
+};
+template <>
+struct SrPack<__nv_bfloat16> {
+    static __device__ __forceinline__ uint16_t pack(float v, uint32_t r) { return sr_pack_bf16(v, r); }
+};
+
 template <typename H>
 struct Store16 {
     static __device__ __forceinline__ Gam load(const void* base, size_t, size_t i) {
@@ -261,6 +295,14 @@ struct Store16 {
         };
         __stcs(reinterpret_cast<uint4*>(base) + i,
                make_uint4(pk(g.ex, g.ey), pk(g.sxx, g.syy), pk(g.sxy, g.pi), pk(g.k, g.W)));
+    }
+    // stochastic rounding: field j takes the 16 bits (r[j / 2] >> 16 (j mod 2)) & 0xFFFF
+    static __device__ __forceinline__ void store_sr(void* base, size_t, size_t i, const Gam& g, uint4 r) {
+        auto pk = [](float lo, float hi, uint32_t w) {
+            return (uint32_t)SrPack<H>::pack(lo, w) | ((uint32_t)SrPack<H>::pack(hi, w >> 16) << 16);
+        };
+        __stcs(reinterpret_cast<uint4*>(base) + i,
+               make_uint4(pk(g.ex, g.ey, r.x), pk(g.sxx, g.syy, r.y), pk(g.sxy, g.pi, r.z), pk(g.k, g.W, r.w)));
     }
 };
 template <>
@@ -297,6 +339,21 @@ struct Work {
         }
     }
 };
+
+// The store of an EM step: round to nearest, or with stochastic_round set and
+// a 16-bit storage type, stochastic rounding from Philox at counter (pixel,
+// frame, 0, 5).
+template <int DT>
+__device__ __forceinline__ void store_step(const Params& P, void* base, size_t hw, size_t i, const Gam& g,
+                                           uint32_t frame) {
+    if constexpr (DT != DT_F32) {
+        if (P.sr) {
+            Store<DT>::store_sr(base, hw, i, g, philox4x32_10(make_uint4((uint32_t)i, frame, 0u, 5u), P.rk));
+            return;
+        }
+    }
+    Store<DT>::store(base, hw, i, g);
+}
 
 __device__ __forceinline__ Gam init_gam(const Params& P) {
     Gam g;

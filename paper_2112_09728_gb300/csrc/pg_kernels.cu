@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void*
     }
     m_step(P, g, st);
     if (!gam_finite(g)) atomicOr(err, 1);
-    Store<DT>::store(gout, hw, (size_t)i, g);
+    store_step<DT>(P, gout, hw, (size_t)i, g, frame);
     if (img) __stcs(img + i, ONE ? f.s : fdiv(f.s, (float)spp));
 }
 
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
     }
     m_step(P, g, st);
     if (!gam_finite(g)) atomicOr(err, 1);
-    Store<DT>::store(gout, hw, (size_t)i, g);
+    store_step<DT>(P, gout, hw, (size_t)i, g, frame);
 }
 
 template <int DT>
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_update(const Params P, const float4*
     }
     m_step(P, g, st);
     if (!gam_finite(g)) atomicOr(err, 1);
-    Store<DT>::store(gout, hw, (size_t)i, g);
+    store_step<DT>(P, gout, hw, (size_t)i, g, P.sr_frame);
 }
 
 template <int DT, bool WORK>

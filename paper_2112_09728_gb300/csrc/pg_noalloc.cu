@@ -106,6 +106,7 @@ extern "C" pg_status pg_frame_noalloc(const pg_config* cfg, const pg_gbuffer* cu
                               st) != cudaSuccess)
         return PG_ERR_CUDA;
     if (pgk::launch_sample(dt, P, work, g0, g1, frame, s, d_img, st) != cudaSuccess) return PG_ERR_CUDA;
+    P.sr_frame = frame;
     if (pgk::launch_update(dt, P, work, g0, g1, s, d_gamma_out, flag, st) != cudaSuccess) return PG_ERR_CUDA;
     return PG_OK;
 }

@@ -78,6 +78,7 @@ pg_status check_config(const pg_config* c, std::string& why) {
     }
     if (c->reuse_radius < 0 || c->reuse_radius > 8) { why = "reuse_radius outside [0, 8]"; return PG_ERR_ARG; }
     if (c->reuse_radius > 0 && c->k_max < 1) { why = "neighbour reuse needs k_max >= 1"; return PG_ERR_ARG; }
+    if (c->stochastic_round != 0 && c->stochastic_round != 1) { why = "stochastic_round must be 0 or 1"; return PG_ERR_ARG; }
     return PG_OK;
 }
 
@@ -115,6 +116,7 @@ void config_params(const pg_config& cfg, Params& P) {
     gauss_legendre(8, P.gl_x + 10, P.gl_w + 10);
     // neighbour reuse: C candidates, walked with the smallest stride >= 0.618 C
     // that is coprime with C (so N <= C picks are distinct)
+    P.sr = cfg.stochastic_round;
     P.reuse_r = cfg.reuse_radius;
     if (cfg.reuse_radius > 0) {
         const int d = 2 * cfg.reuse_radius + 1;

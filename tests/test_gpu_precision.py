@@ -136,3 +136,135 @@ def test_precision_report_small_workload():
     assert report["f32"][0][:6].max() < 2e-4
     assert report["f16"][1][:6].max() < 5e-3
     assert report["bf16"][1][:6].max() < 5e-2
+
+
+# ---------------------------------------------------------------------------
+# Stochastic rounding of the 16-bit store
+# ---------------------------------------------------------------------------
+def _neighbours(v, dtype):
+    """The storage-type neighbours of float64 values v: lo toward zero, hi away."""
+    import torch
+    tt = torch.float16 if dtype == "f16" else torch.bfloat16
+    x = torch.from_numpy(np.asarray(v, np.float64))
+    h = x.to(tt)
+    bits = h.view(torch.int16).to(torch.int32) & 0xFFFF
+    mag = bits & 0x7FFF
+    sign = bits & 0x8000
+    over = h.to(torch.float64).abs() > x.abs()
+    lo_mag = torch.where(over, mag - 1, mag)
+    hi_mag = lo_mag + 1
+
+    def val(m):
+        b = (sign | m).to(torch.int32)
+        b = torch.where(b >= 0x8000, b - 0x10000, b).to(torch.int16)
+        return b.view(tt).to(torch.float64).numpy()
+    lo, hi = val(lo_mag), val(hi_mag)
+    lo = np.where(np.asarray(v) == 0, 0.0, lo)
+    return lo, hi
+
+
+def _sr_reference(v, r16, dtype):
+    """Stochastic rounding from its definition: hi with probability
+    f = (|v| - |lo|) / (|hi| - |lo|), taken as U >= 1 - f for the uniform U
+    the random bits give (13 of them for FP16, all 16 for BF16)."""
+    v = np.asarray(v, np.float64)
+    lo, hi = _neighbours(v, dtype)
+    span = np.abs(hi) - np.abs(lo)
+    f = np.where(span > 0, (np.abs(v) - np.abs(lo)) / np.where(span > 0, span, 1.0), 0.0)
+    u = (r16 >> 3) / 8192.0 if dtype == "f16" else r16 / 65536.0
+    return np.where(u >= 1.0 - f, hi, lo)
+
+
+def _sr_bits(cfg, frame, hw):
+    ctr = np.zeros((hw, 4), np.uint32)
+    ctr[:, 0] = np.arange(hw)
+    ctr[:, 1] = frame
+    ctr[:, 3] = 5
+    w = O.philox(ctr, (cfg.seed_lo, cfg.seed_hi)).astype(np.int64)
+    # field j: bits 16 (j mod 2) and up of word j / 2
+    return np.stack([(w[:, j // 2] >> (16 * (j % 2))) & 0xFFFF for j in range(8)], 1)
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_stochastic_rounding_frame_matches_reference_to_one_ulp(dtype):
+    import dataclasses
+    import torch
+    W, H, spp, frame = 40, 27, 2, 3
+    rng = np.random.default_rng(32)
+    g0, g1 = scenes.random_gbuffer(rng, W, H, rough_lo=0.05)
+    hw = W * H
+    mx, my = rng.uniform(0.05, 0.95, (2, hw))
+    sx, sy = np.exp(rng.uniform(np.log(0.03), np.log(0.4), (2, hw)))
+    rho = rng.uniform(-0.8, 0.8, hw)
+    cen = np.stack([mx, my, sx * sx, sy * sy, rho * sx * sy, rng.uniform(0.05, 0.95, hw),
+                    rng.integers(0, 33, hw).astype(float), rng.uniform(0.1, 3.0, hw)], 1)
+    cen = _round(cen, dtype)
+    par = scenes.Params(W, H, spp=spp, seed=4244)
+    cam = scenes.top_down_camera(pixel_size=0.5)
+    fld = scenes.masked_lobe_field(9, n_lobes=3, kappa_hi=150.0, constant=0.05)
+    from paper_2112_09728_gb300.guide import GuidePass
+    gp = GuidePass(W, H, spp=spp, gamma_dtype=dtype, seed=par.seed, init_pi=par.init_pi, stochastic_round=1)
+    gp.pg_set_gamma(torch.from_numpy(_record_bytes(cen, dtype)).cuda())
+    gp.pg_frame(dev(g0), dev(g1), cam, dev(g0), fld, frame)
+    gp.pg_check()
+    got = _records_to_central(host(gp.pg_get_gamma()), dtype)
+    cfg = ocfg(par)
+    ref_raw, _, s, _ = O.frame(cfg, ocam(cam), ofld(fld), frame, g0, g1, g0, _central_to_raw_moments(cen))
+    ref64 = _raw_to_central(ref_raw)
+    ref = _sr_reference(ref64, _sr_bits(cfg, frame, hw), dtype)
+    ok = ~(s["margin"] < 1e-5).reshape(spp, -1).any(0)
+    d = np.abs(got - ref)[ok]
+    assert (d <= 1.01 * _ulp(ref[ok], dtype)).all(), np.max(d / _ulp(ref[ok], dtype))
+    assert (got[ok, 6] == ref[ok, 6]).all()
+    # the rounding is live: of the fields the update moved, about a quarter
+    # round differently from round-to-nearest (probability min(f, 1 - f))
+    rn = _round(ref64, dtype)
+    moved = (np.abs(ref64 - cen) > 0)[ok]
+    moved[:, 6] = False
+    assert moved.mean() > 0.2
+    assert (got[ok] != rn[ok])[moved].mean() > 0.15
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_stochastic_rounding_is_unbiased_on_the_gpu(dtype):
+    """The same EM update from the same state and samples, rounded with 256
+    different sets of random bits: the mean of the stored values approaches
+    the binary32 update, well inside the half-ulp bias of rounding to
+    nearest."""
+    import torch
+    from paper_2112_09728_gb300.guide import GuidePass
+    W, H, spp, n = 24, 16, 2, 256
+    hw = W * H
+    rng = np.random.default_rng(33)
+    g0, g1 = scenes.random_gbuffer(rng, W, H, rough_lo=0.05)
+    cen = _round(np.stack([rng.uniform(0.1, 0.9, hw), rng.uniform(0.1, 0.9, hw), np.full(hw, 0.02),
+                           np.full(hw, 0.03), np.full(hw, 0.004), rng.uniform(0.2, 0.8, hw),
+                           np.full(hw, 8.0), rng.uniform(0.5, 2.0, hw)], 1), dtype)
+    samples = {k: dev(v) for k, v in scenes.random_samples(rng, spp, hw).items()}
+    cam = scenes.top_down_camera(pixel_size=0.5)
+    fld = scenes.two_lobe_field(4)
+    rec = torch.from_numpy(_record_bytes(cen, dtype)).cuda()
+    acc = np.zeros((hw, 8))
+    for f in range(n):
+        gp = GuidePass(W, H, spp=spp, gamma_dtype=dtype, seed=77, stochastic_round=1)
+        gp.pg_set_gamma(rec)
+        gp.pg_reproject(dev(g0), dev(g1), cam, dev(g0))
+        gp.pg_sample(dev(g0), dev(g1), cam, fld, 1000 + f)     # sets the frame of the rounding bits
+        gp.pg_update(dev(g0), dev(g1), cam, samples)
+        acc += _records_to_central(host(gp.pg_get_gamma()), dtype)
+        gp.close()
+    mean = acc / n
+    # the binary32 update itself, from an FP32 context (same arithmetic, no rounding)
+    gp = GuidePass(W, H, spp=spp, gamma_dtype="f32", seed=77)
+    set_gamma_rows(gp, _central_to_raw_moments(cen))
+    gp.pg_reproject(dev(g0), dev(g1), cam, dev(g0))
+    gp.pg_update(dev(g0), dev(g1), cam, samples)
+    exact = _raw_to_central(get_gamma_rows(gp))
+    moved = np.abs(exact - cen) > 0
+    ulp = _ulp(exact, dtype)
+    # standard deviation of a mean of n roundings is at most ulp / (2 sqrt n)
+    err = np.abs(mean - exact)[moved] / ulp[moved]
+    assert moved[:, :6].mean() > 0.5
+    assert np.max(err) < 5.0 / (2 * np.sqrt(n)) + 0.02, np.max(err)
+    rn_err = np.abs(_round(exact, dtype) - exact)[moved] / ulp[moved]
+    assert rn_err.mean() > 5 * err.mean()
