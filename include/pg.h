@@ -212,6 +212,24 @@ pg_status pg_update(pg_ctx *ctx, const pg_gbuffer *cur, const pg_samples *d_in);
 pg_status pg_frame(pg_ctx *ctx, const pg_gbuffer *cur, const float *d_g0_prev,
                    const pg_field *field, uint32_t frame, float *d_img);
 
+/* A run of whole frames from HOST memory (the end-to-end form of pg_frame;
+ * the paper has no counterpart: it is this library's host pipeline). Frame t
+ * (t < n_frames, frame index frame0 + t) reads h_g0 + t*H*W*4 and
+ * h_g1 + t*H*W*4 (float4 per pixel, as in pg_gbuffer) with cameras[t], its
+ * previous g0 being frame t-1's (for t = 0: h_g0_prev, or its own g0 when
+ * NULL), and writes its per-pixel estimate to h_img + t*H*W (nullable). The
+ * uploads, the frames and the read-backs run on three streams so that
+ * neighbouring frames overlap; device rings of three g0, two g1 and two image
+ * buffers are reused only after the frames that read them have finished.
+ * The call returns when every frame's image is in host memory. Host buffers
+ * should be page-locked (cudaHostAlloc / cudaHostRegister) for the copies to
+ * overlap; pageable memory works but serialises them. Buffers, streams and
+ * events are the context's, created on the first call (PG_ERR_OOM if that
+ * fails). Requires no staged frame in progress. */
+pg_status pg_frames_host(pg_ctx *ctx, int32_t n_frames, const float *h_g0, const float *h_g1,
+                         const pg_camera *cameras, const pg_field *field, uint32_t frame0,
+                         const float *h_g0_prev, float *h_img);
+
 /* Evaluate the current guide (Eq. 2) at n_dirs caller-given world directions
  * per pixel, d_dirs [n_dirs][H*W][3]. d_out [7][n_dirs*H*W] receives p_guide,
  * p_brdf, p_mix (per steradian), the two balance weights, f_r cos and the

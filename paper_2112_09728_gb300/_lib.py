@@ -59,6 +59,8 @@ _SIGNATURES = {
                             C.POINTER(pg_samples), _P]),
     "pg_update": (C.c_int, [_P, C.POINTER(pg_gbuffer), C.POINTER(pg_samples)]),
     "pg_frame": (C.c_int, [_P, C.POINTER(pg_gbuffer), _P, C.POINTER(pg_field), C.c_uint32, _P]),
+    "pg_frames_host": (C.c_int, [_P, C.c_int32, _P, _P, C.POINTER(pg_camera), C.POINTER(pg_field), C.c_uint32,
+                                 _P, _P]),
     "pg_eval": (C.c_int, [_P, C.POINTER(pg_gbuffer), C.POINTER(pg_field), C.c_int32, _P, _P]),
     "pg_gamma_bytes": (C.c_size_t, [_P]),
     "pg_get_gamma": (C.c_int, [_P, _P, C.c_int32]),

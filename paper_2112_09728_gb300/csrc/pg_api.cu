@@ -27,6 +27,14 @@ struct pg_ctx {
     float4* vpl = nullptr;    // neighbour reuse: one VPL per sample {world direction, radiance}
     float* vpl_pb = nullptr;  //   and the density of its BRDF draw (0: does not train)
     float* zbuf = nullptr;    //   and each pixel's rectangle mass Z, from the path-tracing pass
+    // pg_frames_host: device rings for the G-buffer and the image, upload and
+    // read-back streams, and per-step events (created on first use)
+    cudaStream_t hs_up = nullptr, hs_down = nullptr;
+    float4* hg0[3] = {nullptr, nullptr, nullptr};
+    float4* hg1[2] = {nullptr, nullptr};
+    float* himg[2] = {nullptr, nullptr};
+    cudaEvent_t ev_up[4] = {}, ev_ran[4] = {}, ev_down[4] = {};
+    bool host_ready = false;
     pgk::Params base;         // configuration part of the launch parameters
     std::string err;
 };
@@ -67,6 +75,30 @@ size_t hw_of(const pg_ctx* c) { return (size_t)c->cfg.width * c->cfg.height; }
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
     const char *pa = (const char*)a, *pb = (const char*)b;
     return a && b && pa < pb + nb && pb < pa + na;
+}
+
+pg_status ensure_host(pg_ctx* c) {
+    if (c->host_ready) return PG_OK;
+    const size_t hw = hw_of(c);
+    cudaError_t e = cudaStreamCreateWithFlags(&c->hs_up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->hs_down, cudaStreamNonBlocking);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&c->ev_up[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_ran[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_down[k], cudaEventDisableTiming);
+    }
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->hg0[k], hw * sizeof(float4));
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&c->hg1[k], hw * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc(&c->himg[k], hw * sizeof(float));
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PG_ERR_OOM, std::string("pg_frames_host: cannot set up the host pipeline: ") +
+                                       cudaGetErrorString(e));
+    }
+    c->host_ready = true;
+    return PG_OK;
 }
 
 pg_status ensure_work(pg_ctx* c) {
@@ -217,16 +249,14 @@ pg_status pg_update(pg_ctx* c, const pg_gbuffer* cur, const pg_samples* d_in) {
     return PG_OK;
 }
 
-pg_status pg_frame(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, const pg_field* field,
-                   uint32_t frame, float* d_img) {
-    if (!c) return PG_ERR_ARG;
-    if (c->phase != 0) return fail(c, PG_ERR_STATE, "pg_frame: a staged frame is in progress");
-    pg_status s = check_gbuffer(c, cur);
-    if (s != PG_OK) return s;
-    if (!d_g0_prev || !aligned16(d_g0_prev)) return fail(c, PG_ERR_ARG, "d_g0_prev NULL or not 16-byte aligned");
-    const size_t hw = hw_of(c);
-    if (overlaps(d_img, hw * 4, c->gam[0], c->gam_bytes) || overlaps(d_img, hw * 4, c->gam[1], c->gam_bytes))
-        return fail(c, PG_ERR_ARG, "d_img overlaps Gamma");
+}  // extern "C"
+
+namespace {
+
+// The launches of one frame on the context's stream (arguments checked by the caller).
+pg_status frame_impl(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, const pg_field* field,
+                     uint32_t frame, float* d_img) {
+    pg_status s;
     pgk::Params P = c->base;
     if ((s = fill_camera(c, cur->camera, P)) != PG_OK || (s = fill_field(c, field, P)) != PG_OK) return s;
     const float4 *g0 = (const float4*)cur->g0, *g1 = (const float4*)cur->g1, *g0p = (const float4*)d_g0_prev;
@@ -244,6 +274,78 @@ pg_status pg_frame(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, con
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "pg_frame");
     c->cur ^= 1;
+    return PG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pg_status pg_frame(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, const pg_field* field,
+                   uint32_t frame, float* d_img) {
+    if (!c) return PG_ERR_ARG;
+    if (c->phase != 0) return fail(c, PG_ERR_STATE, "pg_frame: a staged frame is in progress");
+    pg_status s = check_gbuffer(c, cur);
+    if (s != PG_OK) return s;
+    if (!d_g0_prev || !aligned16(d_g0_prev)) return fail(c, PG_ERR_ARG, "d_g0_prev NULL or not 16-byte aligned");
+    const size_t hw = hw_of(c);
+    if (overlaps(d_img, hw * 4, c->gam[0], c->gam_bytes) || overlaps(d_img, hw * 4, c->gam[1], c->gam_bytes))
+        return fail(c, PG_ERR_ARG, "d_img overlaps Gamma");
+    return frame_impl(c, cur, d_g0_prev, field, frame, d_img);
+}
+
+pg_status pg_frames_host(pg_ctx* c, int32_t n_frames, const float* h_g0, const float* h_g1,
+                         const pg_camera* cameras, const pg_field* field, uint32_t frame0, const float* h_g0_prev,
+                         float* h_img) {
+    if (!c) return PG_ERR_ARG;
+    if (c->phase != 0) return fail(c, PG_ERR_STATE, "pg_frames_host: a staged frame is in progress");
+    if (n_frames < 1 || n_frames > (1 << 20)) return fail(c, PG_ERR_ARG, "pg_frames_host: n_frames outside [1, 2^20]");
+    if (!h_g0 || !h_g1 || !cameras) return fail(c, PG_ERR_ARG, "pg_frames_host: h_g0, h_g1 and cameras are required");
+    pg_status s = ensure_host(c);
+    if (s != PG_OK) return s;
+    const size_t hw = hw_of(c), gbytes = hw * sizeof(float4), ibytes = hw * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    // step t: upload into g0 slot t % 3 and g1 slot t % 2, once step t-2 (the
+    // last reader of both slots) has run; run once the upload is in and step
+    // t-2's image has been read back; read back once the step has run.
+    if (h_g0_prev) e = cudaMemcpyAsync(c->hg0[2], h_g0_prev, gbytes, cudaMemcpyHostToDevice, c->hs_up);
+    for (int32_t t = 0; t < n_frames && e == cudaSuccess; ++t) {
+        const int a = t % 3, b = t % 2, k = t % 4, k2 = (t + 2) % 4;   // k2: the events of step t - 2
+        if (t >= 2) e = cudaStreamWaitEvent(c->hs_up, c->ev_ran[k2], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->hg0[a], h_g0 + (size_t)t * hw * 4, gbytes, cudaMemcpyHostToDevice, c->hs_up);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->hg1[b], h_g1 + (size_t)t * hw * 4, gbytes, cudaMemcpyHostToDevice, c->hs_up);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_up[k], c->hs_up);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_up[k], 0);
+        if (e == cudaSuccess && t >= 2 && h_img) e = cudaStreamWaitEvent(c->stream, c->ev_down[k2], 0);
+        if (e != cudaSuccess) break;
+        pg_gbuffer gb;
+        gb.g0 = reinterpret_cast<const float*>(c->hg0[a]);
+        gb.g1 = reinterpret_cast<const float*>(c->hg1[b]);
+        gb.camera = cameras[t];
+        const float4* prev = t > 0 ? c->hg0[(t + 2) % 3] : (h_g0_prev ? c->hg0[2] : c->hg0[a]);
+        s = frame_impl(c, &gb, reinterpret_cast<const float*>(prev), field, frame0 + (uint32_t)t,
+                       h_img ? c->himg[b] : nullptr);
+        if (s != PG_OK) {
+            cudaStreamSynchronize(c->hs_up);
+            cudaStreamSynchronize(c->stream);
+            cudaStreamSynchronize(c->hs_down);
+            return s;
+        }
+        e = cudaEventRecord(c->ev_ran[k], c->stream);
+        if (e == cudaSuccess && h_img) {
+            e = cudaStreamWaitEvent(c->hs_down, c->ev_ran[k], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_img + (size_t)t * hw, c->himg[b], ibytes, cudaMemcpyDeviceToHost, c->hs_down);
+            if (e == cudaSuccess) e = cudaEventRecord(c->ev_down[k], c->hs_down);
+        }
+    }
+    const cudaError_t e1 = cudaStreamSynchronize(c->hs_up);
+    const cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    const cudaError_t e3 = cudaStreamSynchronize(c->hs_down);
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pg_frames_host");
     return PG_OK;
 }
 
@@ -407,6 +509,19 @@ void pg_destroy(pg_ctx* c) {
     if (c->vpl) cudaFree(c->vpl);
     if (c->vpl_pb) cudaFree(c->vpl_pb);
     if (c->zbuf) cudaFree(c->zbuf);
+    for (int k = 0; k < 3; ++k)
+        if (c->hg0[k]) cudaFree(c->hg0[k]);
+    for (int k = 0; k < 2; ++k) {
+        if (c->hg1[k]) cudaFree(c->hg1[k]);
+        if (c->himg[k]) cudaFree(c->himg[k]);
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (c->ev_up[k]) cudaEventDestroy(c->ev_up[k]);
+        if (c->ev_ran[k]) cudaEventDestroy(c->ev_ran[k]);
+        if (c->ev_down[k]) cudaEventDestroy(c->ev_down[k]);
+    }
+    if (c->hs_up) cudaStreamDestroy(c->hs_up);
+    if (c->hs_down) cudaStreamDestroy(c->hs_down);
     delete c;
 }
 

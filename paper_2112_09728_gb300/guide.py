@@ -167,6 +167,31 @@ class GuidePass:
                    C.c_void_p(_ptr(g0_prev, what="g0_prev", align16=True)), C.byref(make_field(field)),
                    C.c_uint32(int(frame) & 0xFFFFFFFF), C.c_void_p(_ptr(img, what="img")))
 
+    def pg_frames_host(self, g0, g1, cameras, field, frame0, g0_prev=None, img=None):
+        """n whole frames from host memory: g0, g1 CPU float32 tensors [n, H*W, 4]
+        (page-locked for overlapped copies), cameras a list of n cameras,
+        g0_prev the g0 before frame 0 (CPU [H*W, 4] or None), img a CPU float32
+        tensor [n, H*W] for the estimates (or None). Returns img."""
+        n = len(cameras)
+        for t, what in ((g0, "g0"), (g1, "g1")):
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+                raise TypeError("%s must be a contiguous float32 CPU tensor" % what)
+            self._check_len(t, n * 4 * self.hw, what)
+        if g0_prev is not None:
+            if g0_prev.is_cuda or g0_prev.dtype != torch.float32 or not g0_prev.is_contiguous():
+                raise TypeError("g0_prev must be a contiguous float32 CPU tensor")
+            self._check_len(g0_prev, 4 * self.hw, "g0_prev")
+        if img is not None:
+            if img.is_cuda or img.dtype != torch.float32 or not img.is_contiguous():
+                raise TypeError("img must be a contiguous float32 CPU tensor")
+            self._check_len(img, n * self.hw, "img")
+        cams = (L.pg_camera * n)(*[make_camera(c) for c in cameras])
+        self._call("pg_frames_host", C.c_int32(n), C.c_void_p(g0.data_ptr()), C.c_void_p(g1.data_ptr()), cams,
+                   C.byref(make_field(field)), C.c_uint32(int(frame0) & 0xFFFFFFFF),
+                   C.c_void_p(None if g0_prev is None else g0_prev.data_ptr()),
+                   C.c_void_p(None if img is None else img.data_ptr()))
+        return img
+
     def pg_eval(self, g0, g1, camera, field, dirs, out=None):
         """dirs [n, H*W, 3] float32 -> dict of [n, H*W] planes (EVAL_KEYS)."""
         n = dirs.numel() // (3 * self.hw)

@@ -96,3 +96,37 @@ def test_out_of_order_calls_are_refused():
     odd = torch.zeros(W * H * 4 + 1, device="cuda")[1:]
     with pytest.raises((_lib.PgError, ValueError)):
         gp.pg_frame(odd, dev(g1), cam, dev(g0), fld, 0)
+
+
+@pytest.mark.parametrize("pinned,reuse", [(True, 0), (False, 0), (True, 2)])
+def test_frames_from_host_memory_equal_frame_by_frame(pinned, reuse):
+    """pg_frames_host (uploads, frames and read-backs overlapped on three
+    streams) gives the same Gamma and images, bit for bit, as pg_frame called
+    frame by frame on device copies of the same inputs."""
+    import dataclasses
+    import torch
+    n = 7
+    wl = scenes.workload_pan(96, 40, frames=n)
+    par = dataclasses.replace(wl["params"], reuse_radius=reuse)
+    fld, sc = wl["field"], wl["scene"]
+    hw = par.width * par.height
+    g0h = torch.stack([torch.from_numpy(sc.gbuffer(t)[0]) for t in range(n)]).contiguous()
+    g1h = torch.stack([torch.from_numpy(sc.gbuffer(t)[1]) for t in range(n)]).contiguous()
+    if pinned:
+        g0h, g1h = g0h.pin_memory(), g1h.pin_memory()
+    imgh = torch.zeros((n, hw), pin_memory=pinned)
+    cams = [sc.camera(t) for t in range(n)]
+    a = guide(par, "f16")
+    a.pg_frames_host(g0h, g1h, cams, fld, 0, img=imgh)
+    b = guide(par, "f16")
+    img = torch.empty(hw, device="cuda")
+    for t in range(n):
+        g0, g1, g0p = (dev(x) for x in sc.gbuffer(t))
+        b.pg_frame(g0, g1, cams[t], g0p, fld, t, img)
+        assert torch.equal(imgh[t], img.cpu()), t
+    assert torch.equal(a.pg_get_gamma(), b.pg_get_gamma())
+    # continuing from a given previous g0
+    a.pg_frames_host(g0h[n - 1:], g1h[n - 1:], cams[n - 1:], fld, n, g0_prev=g0h[n - 2].contiguous())
+    g0, g1, g0p = (dev(x) for x in sc.gbuffer(n - 1))
+    b.pg_frame(g0, g1, cams[n - 1], g0p, fld, n)
+    assert torch.equal(a.pg_get_gamma(), b.pg_get_gamma())
