@@ -234,8 +234,14 @@ struct HalfStore {
 };
 template <>
 __device__ __forceinline__ float HalfStore<__half>::cvt(uint16_t v) { return __half2float(__ushort_as_half(v)); }
+// FP16 saturates at +-65504 rather than overflowing to infinity: the mass W
+// can pass it under neighbour reuse, whose importance weights f / p_src are
+// unbounded. (The finiteness check runs on the binary32 values before the
+// store, so a NaN is still reported.)
 template <>
-__device__ __forceinline__ uint16_t HalfStore<__half>::pack(float v) { return __half_as_ushort(__float2half_rn(v)); }
+__device__ __forceinline__ uint16_t HalfStore<__half>::pack(float v) {
+    return __half_as_ushort(__float2half_rn(fminf(fmaxf(v, -65504.0f), 65504.0f)));
+}
 template <>
 __device__ __forceinline__ float HalfStore<__nv_bfloat16>::cvt(uint16_t v) {
     return __bfloat162float(__ushort_as_bfloat16(v));
@@ -250,7 +256,8 @@ __device__ __forceinline__ uint16_t HalfStore<__nv_bfloat16>::pack(float v) {
 // proportional to proximity, so the stored value is v in expectation (an EM
 // update below half a storage ulp still moves the guide on average).
 // FP16: |v| + u ulp16(|v|), u = (r >> 3) / 2^13, then toward zero; the sum is
-// exact in binary32 (u ulp16 is a multiple of binary32's ulp at |v|).
+// exact in binary32 (u ulp16 is a multiple of binary32's ulp at |v|), and
+// rounding toward zero saturates at 65504 like the nearest-rounding store.
 // BF16: the random bits are added below bf16's last kept bit, then the low
 // half is dropped (a carry rounds the magnitude up).
 __device__ __forceinline__ uint16_t sr_pack_f16(float v, uint32_t r) {

@@ -22,9 +22,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _round(x, dtype):
+    """Round to nearest in the storage type; FP16 saturates at +-65504 as the store does."""
     import torch
     t = torch.from_numpy(np.asarray(x, np.float64))
-    return (t.to(torch.float16) if dtype == "f16" else t.to(torch.bfloat16)).to(torch.float64).numpy()
+    if dtype == "f16":
+        return t.clamp(-65504.0, 65504.0).to(torch.float16).to(torch.float64).numpy()
+    return t.to(torch.bfloat16).to(torch.float64).numpy()
 
 
 def _ulp(x, dtype):
