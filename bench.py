@@ -466,6 +466,31 @@ def run_temporal(width=1920, height=1080, frames=60, tail=30):
     return out
 
 
+def orbit_step(width, height, frames=4):
+    """Runs `frames` steps of the orbit workload (EM frame at 4 spp, adjoint,
+    Adam; FP16 Gamma) at the given size and prints nothing but a status line:
+    the program the orbit kernels' ncu captures run at a reduced size."""
+    import torch
+    import __graft_entry__
+    from paper_2112_09728_gb300 import scenes
+    from paper_2112_09728_gb300.guide import GuidePass
+    __graft_entry__.build()
+    wl = scenes.workload_4k(width, height)
+    par, fld, sc = wl["params"], wl["field"], wl["scene"]
+    gp = GuidePass(width, height, spp=par.spp, gamma_dtype="f16", seed=par.seed, init_pi=par.init_pi)
+    hw = width * height
+    img, loss = torch.empty(hw, device="cuda"), torch.empty(hw, device="cuda")
+    grad = torch.empty((6, hw), device="cuda")
+    for t in range(frames):
+        g0, g1, g0p = sc.gbuffer_on(t, "cuda")
+        gp.pg_frame(g0, g1, sc.camera(t), g0p, fld, t, img)
+        gp.pg_grad(g0, g1, sc.camera(t), fld, t, par.spp, loss=loss, grad=grad)
+        gp.pg_adam_step(grad, lr=1e-2, step=t + 1)
+    torch.cuda.synchronize()
+    gp.pg_check()
+    print("orbit step ok: %dx%d, %d frames" % (width, height, frames), file=sys.stderr)
+
+
 def run_diff(width=512, height=512, spp=64, steps=20, lr=1e-2, eval_frames=4, ref_spp=256):
     """Differentiation form against EM at equal samples: two FP32 guides start
     from the same state; one takes `steps` EM steps (the fused pass at `spp`
@@ -644,11 +669,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 EM + gradient-step leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the 512x512 Adam-versus-EM comparison")
+    ap.add_argument("--orbit-step", default=None, metavar="WxH",
+                    help="run four steps of the orbit workload at WxH and exit (the program of its ncu captures)")
     ap.add_argument("--no-temporal", action="store_true",
                     help="skip the static-camera temporal-stability and the stochastic-rounding legs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.orbit_step:
+        w, h = (int(v) for v in args.orbit_step.lower().split("x"))
+        orbit_step(w, h)
+        return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -761,7 +761,11 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
 //   dPhi2/drho = exp(-(h^2 - 2 rho h k + k^2)/(2(1-rho^2))) / (2 pi sqrt(1-rho^2)),
 // chained through h = (a - mu_x)/s_x, k = (b - mu_y)/s_y, rho = s_xy/(s_x s_y).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float normal_cdf(float x) { return 0.5f * erfcf(-x * 0.70710678118654752f); }
+// Phi(x) from the fitted upper tail (normal_tail): within 2e-7 absolute.
+__device__ __forceinline__ float normal_cdf(float x) {
+    const float t = normal_tail(fabsf(x));
+    return x >= 0.0f ? 1.0f - t : t;
+}
 
 __device__ __forceinline__ void rect_mass_grad(const Guide& d, float dz[5]) {
     const float isx = d.il11, isy = rsqrtf(d.syy);
