@@ -46,7 +46,7 @@ class Config(C.Structure):
                 ("depth_tol", C.c_double), ("normal_tol", C.c_double),
                 ("rough_min", C.c_double), ("sigma2_min", C.c_double), ("rho_max", C.c_double),
                 ("init_mu", C.c_double * 2), ("init_sigma", C.c_double * 3),
-                ("reuse_radius", C.c_int32)]
+                ("reuse_radius", C.c_int32), ("ggx_f0", C.c_double)]
 
 
 class Camera(C.Structure):
@@ -99,6 +99,8 @@ def _load():
                 "or_adam": [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double,
                             C.c_double, C.c_double, C.c_double],
                 "or_reuse_picks": [_P, C.c_double, C.c_uint32, C.c_uint32, _P, _P, _P],
+                "or_brdf_cos_f0": [C.c_double, C.c_double, C.c_double, _P, _P],
+                "or_dielectric_fresnel": [C.c_double],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -111,6 +113,8 @@ def _load():
             lib.or_brdf_sample.restype = C.c_int
             lib.or_radiance.restype = C.c_double
             lib.or_reuse_picks.restype = C.c_int
+            lib.or_brdf_cos_f0.restype = C.c_double
+            lib.or_dielectric_fresnel.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -135,7 +139,7 @@ def _f32(a, shape=None):
 def make_config(width, height, spp=1, seed=0, k_max=32, pi_min=0.05, pi_max=0.95,
                 pi_reinit=0.05, depth_tol=0.1, normal_tol=0.9, rough_min=0.1,
                 sigma2_min=1e-4, rho_max=0.9, init_mu=(0.5, 0.5),
-                init_sigma=(0.1, 0.1, 0.0), reuse_radius=0) -> Config:
+                init_sigma=(0.1, 0.1, 0.0), reuse_radius=0, ggx_f0=1.0) -> Config:
     """Thresholds that the GPU applies in binary32 are rounded to binary32 here
     so that both sides compare against the same number."""
     f32 = lambda v: float(np.float32(v))
@@ -148,6 +152,7 @@ def make_config(width, height, spp=1, seed=0, k_max=32, pi_min=0.05, pi_max=0.95
     c.init_mu[:] = [f32(v) for v in init_mu]
     c.init_sigma[:] = [f32(v) for v in init_sigma]
     c.reuse_radius = int(reuse_radius)
+    c.ggx_f0 = f32(ggx_f0)
     return c
 
 
@@ -241,6 +246,15 @@ def rect_mass_grad(g5):
 def brdf_cos(rough, albedo, wo, wi):
     return _load().or_brdf_cos(float(rough), float(albedo), _ptr(_f64(wo, (3,))),
                                _ptr(_f64(wi, (3,))))
+
+
+def brdf_cos_f0(rough, albedo, f0, wo, wi):
+    return _load().or_brdf_cos_f0(float(rough), float(albedo), float(f0), _ptr(_f64(wo, (3,))),
+                                  _ptr(_f64(wi, (3,))))
+
+
+def dielectric_fresnel(ci):
+    return _load().or_dielectric_fresnel(float(ci))
 
 
 def brdf_pdf(rough, wo, wi):

@@ -42,6 +42,7 @@ typedef struct {
     double depth_tol, normal_tol, rough_min, sigma2_min, rho_max;
     double init_mu[2], init_sigma[3];
     int32_t reuse_radius;    /* neighbour-VPL reuse window radius R (0: off) */
+    double ggx_f0;           /* Schlick reflectance of GGX at normal incidence (1: F = 1) */
 } or_config;
 
 typedef struct {
@@ -66,7 +67,7 @@ typedef struct {
     double *pdf;             /* mixture pdf p_mix(w), solid angle */
     double *mis;             /* balance-heuristic weight of the drawing strategy */
     double *estimate;        /* F = L f_r cos / p_mix (0 for an invalid draw) */
-    uint8_t *strategy;       /* 0 BRDF, 1 guide, 2 guide draw outside the square -> BRDF */
+    uint8_t *strategy;       /* 0 BRDF, 1 guide, 2 guide draw outside the square -> BRDF, 3 transparent delta */
     double *pg, *pb;         /* guide and BRDF pdfs (solid angle) at w */
     double *ux, *uy;         /* square coordinates used for the guide pdf */
     double *margin;          /* distance of the sample's own decisions to their thresholds */
@@ -74,7 +75,7 @@ typedef struct {
 
 /* strategy byte: low two bits name the strategy, bit 2 marks a wasted draw
  * (a GGX reflection below the horizon), which contributes nothing */
-enum { S_BRDF = 0, S_GUIDE = 1, S_FALLBACK = 2, S_INVALID = 4 };
+enum { S_BRDF = 0, S_GUIDE = 1, S_FALLBACK = 2, S_DELTA = 3, S_INVALID = 4 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
@@ -337,13 +338,33 @@ void or_rect_mass_grad_many(int64_t n, const double *g5, double *dz)
 
 /* ------------------------------------------------------------------------ */
 /* Materials (Eq. 1's f_r). The paper does not define its BRDFs; the        */
-/* synthetic scenes use a Lambertian surface (f_r = albedo/pi) and a GGX    */
+/* synthetic scenes use a Lambertian surface (f_r = albedo/pi), a GGX       */
 /* microfacet surface (Walter et al. 2007: alpha = roughness^2, separable   */
-/* Smith shadowing, Fresnel taken as 1, visible normals not used; the draw  */
-/* picks the half vector with density D(h) cos(theta_h) and reflects the    */
-/* view direction about it). rough < 0 marks a Lambertian pixel.            */
+/* Smith shadowing, Schlick's Fresnel F = F0 + (1 - F0)(1 - o.h)^5 with F0  */
+/* from the configuration, F0 = 1 giving F = 1; visible normals not used;   */
+/* the draw picks the half vector with density D(h) cos(theta_h) and        */
+/* reflects the view direction about it) and a transparent surface (Sec. 5: */
+/* guiding is off for transparent materials): a smooth dielectric of index  */
+/* 1.5 that reflects or refracts the view direction, choosing reflection    */
+/* with its exact unpolarised Fresnel reflectance, tinted by the albedo.    */
+/* The roughness slot codes the material: >= 0 GGX, in (-1.5, 0) Lambertian */
+/* (-1 by convention), <= -1.5 transparent (-2 by convention).              */
 /* All directions are in the local frame (normal = +z).                     */
 /* ------------------------------------------------------------------------ */
+static int is_transparent(double rough) { return rough <= -1.5; }
+static int is_lambert(double rough) { return rough < 0.0 && rough > -1.5; }
+
+#define DIELECTRIC_IOR 1.5
+
+/* Unpolarised Fresnel reflectance of a smooth dielectric for light arriving
+ * from outside at cosine ci > 0 (no total reflection from the outside). */
+double or_dielectric_fresnel(double ci)
+{
+    double n = DIELECTRIC_IOR, si2 = 1.0 - ci * ci, ct = sqrt(1.0 - si2 / (n * n));
+    double rs = (ci - n * ct) / (ci + n * ct), rp = (n * ci - ct) / (n * ci + ct);
+    return 0.5 * (rs * rs + rp * rp);
+}
+
 static double ggx_alpha(double rough) { double a = rough * rough; return a < 1e-4 ? 1e-4 : a; }
 
 static double ggx_d(double a2, double nh)
@@ -357,22 +378,30 @@ static double smith_g1(double a2, double c)
     return 2.0 * c / (c + sqrt(a2 + (1.0 - a2) * c * c));
 }
 
-/* f_r * cos(theta_i). */
-double or_brdf_cos(double rough, double albedo, const double wo[3], const double wi[3])
+/* f_r * cos(theta_i) with GGX reflectance f0 at normal incidence (0 for a
+ * transparent surface: its BSDF is a pair of deltas). */
+double or_brdf_cos_f0(double rough, double albedo, double f0, const double wo[3], const double wi[3])
 {
-    if (wi[2] <= 0.0 || wo[2] <= 0.0) return 0.0;
+    if (wi[2] <= 0.0 || wo[2] <= 0.0 || is_transparent(rough)) return 0.0;
     if (rough < 0.0) return albedo / M_PI * wi[2];
     double a = ggx_alpha(rough), a2 = a * a;
     double h[3] = {wo[0] + wi[0], wo[1] + wi[1], wo[2] + wi[2]};
     double hl = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
     double nh = h[2] / hl;
-    return albedo * ggx_d(a2, nh) * smith_g1(a2, wi[2]) * smith_g1(a2, wo[2]) / (4.0 * wo[2]);
+    double oh = (wo[0] * h[0] + wo[1] * h[1] + wo[2] * h[2]) / hl;
+    double m = 1.0 - oh, fr = f0 + (1.0 - f0) * m * m * m * m * m;
+    return albedo * fr * ggx_d(a2, nh) * smith_g1(a2, wi[2]) * smith_g1(a2, wo[2]) / (4.0 * wo[2]);
+}
+
+double or_brdf_cos(double rough, double albedo, const double wo[3], const double wi[3])
+{
+    return or_brdf_cos_f0(rough, albedo, 1.0, wo, wi);
 }
 
 /* Density of the BRDF draw at wi (solid angle). */
 double or_brdf_pdf(double rough, const double wo[3], const double wi[3])
 {
-    if (wi[2] <= 0.0) return 0.0;
+    if (wi[2] <= 0.0 || is_transparent(rough)) return 0.0;
     if (rough < 0.0) return wi[2] / M_PI;
     if (wo[2] <= 0.0) return 0.0;
     double a = ggx_alpha(rough), a2 = a * a;
@@ -386,10 +415,29 @@ double or_brdf_pdf(double rough, const double wo[3], const double wi[3])
 
 /* BRDF draw from two uniforms in [0,1). Returns 1 for a draw in the upper
  * hemisphere, 0 for a wasted draw; *margin receives how far the validity
- * decision was from its threshold. */
+ * decision was from its threshold. A transparent surface reflects when
+ * x1 < F (the Fresnel reflectance at the view direction) and refracts
+ * otherwise, into the lower hemisphere; a view from below wastes the draw. */
 int or_brdf_sample(double rough, const double wo[3], double x1, double x2, double wi[3],
                    double *margin)
 {
+    if (is_transparent(rough)) {
+        double ci = wo[2];
+        if (ci <= 0.0) {
+            wi[0] = wi[1] = 0.0; wi[2] = 1.0;
+            *margin = fabs(ci);
+            return 0;
+        }
+        double fr = or_dielectric_fresnel(ci), eta = 1.0 / DIELECTRIC_IOR;
+        *margin = fabs(x1 - fr) < ci ? fabs(x1 - fr) : ci;
+        if (x1 < fr) {
+            wi[0] = -wo[0]; wi[1] = -wo[1]; wi[2] = ci;
+        } else {
+            double ct = sqrt(1.0 - eta * eta * (1.0 - ci * ci));
+            wi[0] = -eta * wo[0]; wi[1] = -eta * wo[1]; wi[2] = -ct;
+        }
+        return 1;
+    }
     if (rough < 0.0) {
         /* cosine-weighted: radius sqrt(x1) on the disk, lifted */
         double r = sqrt(x1), phi = 2.0 * M_PI * x2;
@@ -609,7 +657,7 @@ void or_reproject(const or_config *cfg, const float *g0, const float *g1, const 
 typedef struct {
     double g5[5], chol[3], Z, pi_eff;
     double n[3], wo_l[3], pos[3];
-    double rough, albedo;
+    double rough, albedo, f0;
 } pixel_ctx;
 
 static void cholesky(const double g5[5], double c[3])
@@ -633,12 +681,14 @@ static void pixel_setup(const or_config *cfg, const or_camera *cam, int x, int y
     to_local(p->n, wo, p->wo_l);
     p->rough = g1[4 * i + 2];
     p->albedo = g1[4 * i + 3];
+    p->f0 = cfg->ggx_f0;
     derive_gauss(cfg, gm, p->g5);
     cholesky(p->g5, p->chol);
     p->Z = or_rect_mass(p->g5);
-    /* Guiding is off on a re-initialised pixel (Sec. 3.1) and on near-mirror
-     * surfaces (Sec. 5; threshold rough_min is this build's reading). */
-    int gated = reinit || (p->rough >= 0.0 && p->rough < cfg->rough_min);
+    /* Guiding is off on a re-initialised pixel (Sec. 3.1), on near-mirror
+     * surfaces (Sec. 5; threshold rough_min is this build's reading) and on
+     * transparent surfaces (Sec. 5). */
+    int gated = reinit || (p->rough >= 0.0 && p->rough < cfg->rough_min) || is_transparent(p->rough);
     p->pi_eff = gated ? 0.0 : gm[G_PI];
 }
 
@@ -659,7 +709,7 @@ static void eval_local(const or_field *fld, const pixel_ctx *p, const double wl[
     double u[2];
     if (u_in) { u[0] = u_in[0]; u[1] = u_in[1]; } else or_hemi_to_square(wl, u);
     u_out[0] = u[0]; u_out[1] = u[1];
-    *fcos = *rad * or_brdf_cos(p->rough, p->albedo, p->wo_l, wl);
+    *fcos = *rad * or_brdf_cos_f0(p->rough, p->albedo, p->f0, p->wo_l, wl);
     *pb = or_brdf_pdf(p->rough, p->wo_l, wl);
     *pg = or_gauss_pdf(p->g5, u) / (2.0 * M_PI);
     *pmix = p->pi_eff * *pg + (1.0 - p->pi_eff * p->Z) * *pb;
@@ -706,7 +756,8 @@ static int draw_direction(const pixel_ctx *p, const uint32_t key[2], uint32_t pi
             if (mb < *margin) *margin = mb;
         }
     } else {
-        strat = S_BRDF;
+        /* a transparent surface (always gated) draws one of its two deltas */
+        strat = is_transparent(p->rough) ? S_DELTA : S_BRDF;
         double mb;
         *valid = or_brdf_sample(p->rough, p->wo_l, unif(r0[1]), unif(r0[2]), wl, &mb);
         if (mb < *margin) *margin = mb;
@@ -731,18 +782,27 @@ static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_fi
         int strat = draw_direction(&p, key, (uint32_t)i, frame, (uint32_t)s, 0u, wl, u, &have_u, &valid,
                                    &margin);
         double fcos = 0, pg = 0, pb = 0, pmix = 0, rad, uo[2] = {-1.0, -1.0};
-        if (valid) {
+        double F = 0.0, mis = 0.0;
+        if (valid && strat == S_DELTA) {
+            /* a delta of the transparent surface: the Fresnel weight of the
+             * chosen branch cancels its probability, leaving the tint */
+            double wwi[3];
+            to_world(p.n, wl, wwi);
+            rad = or_radiance(fld, p.pos, wwi);
+            F = p.albedo * rad;
+            mis = 1.0;
+        } else if (valid) {
             eval_local(fld, &p, wl, have_u ? u : NULL, &fcos, &pg, &pb, &pmix, &rad, uo);
+            if (pmix > 0.0) {
+                F = fcos / pmix;
+                mis = strat == S_GUIDE ? p.pi_eff * pg / pmix : (1.0 - p.pi_eff * p.Z) * pb / pmix;
+            }
         } else {
             double wwi[3];
             to_world(p.n, wl, wwi);
             rad = or_radiance(fld, p.pos, wwi);
             strat |= S_INVALID;
         }
-        double F = (valid && pmix > 0.0) ? fcos / pmix : 0.0;
-        double mis = 0.0;
-        if (valid && pmix > 0.0)
-            mis = strat == S_GUIDE ? p.pi_eff * pg / pmix : (1.0 - p.pi_eff * p.Z) * pb / pmix;
         double ww[3];
         to_world(p.n, wl, ww);
         if (S->wx) { S->wx[o] = ww[0]; S->wy[o] = ww[1]; S->wz[o] = ww[2]; }
@@ -814,7 +874,7 @@ static void update_pixel(const or_config *cfg, const or_camera *cam, int x, int 
         if (wl[2] <= 0.0) continue;
         double u[2];
         or_hemi_to_square(wl, u);
-        double fcos = rad[o] * or_brdf_cos(p.rough, p.albedo, p.wo_l, wl);
+        double fcos = rad[o] * or_brdf_cos_f0(p.rough, p.albedo, p.f0, p.wo_l, wl);
         double pb = or_brdf_pdf(p.rough, p.wo_l, wl);
         if (!(pb > 0.0)) continue;
         double pg = or_gauss_pdf(p.g5, u) / (2.0 * M_PI);
@@ -949,7 +1009,7 @@ static void vpl_stats(const pixel_ctx *p, const double ww[3], double L, double p
     if (wl[2] <= 0.0 || !(pb_src > 0.0)) return;
     double u[2];
     or_hemi_to_square(wl, u);
-    double fcos = L * or_brdf_cos(p->rough, p->albedo, p->wo_l, wl);
+    double fcos = L * or_brdf_cos_f0(p->rough, p->albedo, p->f0, p->wo_l, wl);
     double pb = or_brdf_pdf(p->rough, p->wo_l, wl);
     double pg = or_gauss_pdf(p->g5, u) / (2.0 * M_PI);
     double pmix = p->pi_eff * pg + (1.0 - p->pi_eff * p->Z) * pb;

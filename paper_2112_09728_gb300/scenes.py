@@ -62,6 +62,7 @@ class Params:
     init_sigma: tuple = (0.1, 0.1, 0.0)
     init_pi: float = 0.5
     reuse_radius: int = 0      # neighbour-VPL reuse window radius (0: off)
+    ggx_f0: float = 1.0        # Schlick reflectance of GGX at normal incidence (1: no Fresnel)
 
 
 def unit_hemisphere_dirs(rng, n, zmin=0.0):
