@@ -86,7 +86,12 @@ typedef enum { PG_F32 = 0, PG_F16 = 1, PG_BF16 = 2 } pg_dtype;
  * smaller than half a storage ulp then still moves the guide on average.
  * pg_update takes `frame` from the pg_sample of its staged frame (0 without
  * one). Values
- * that are already representable are stored exactly either way. */
+ * that are already representable are stored exactly either way.
+ * ggx_f0 [1] Schlick reflectance of the GGX lobe at normal incidence, in
+ * [0, 1]: f_r carries F = F0 + (1 - F0)(1 - o.h)^5; 1 gives F = 1.
+ * transparent [0] 1 enables the transparent material (roughness codes
+ * <= -1.5, see pg_gbuffer); with 0 every negative roughness code is
+ * Lambertian and the fused kernel carries none of the transparent code. */
 typedef struct {
     int32_t width, height;   /* screen size in pixels, each in [1, 32768] */
     int32_t spp;             /* samples per pixel per frame, in [1, 1024] */
@@ -98,6 +103,8 @@ typedef struct {
     float init_mu[2], init_sigma[3], init_pi;
     int32_t reuse_radius;
     int32_t stochastic_round;
+    float ggx_f0;
+    int32_t transparent;
 } pg_config;
 
 /* Camera of one frame: the primary ray of pixel (x, y). Orthographic (kind 0):
@@ -116,8 +123,15 @@ typedef struct {
  * arrays of width*height elements, 16-byte aligned.
  *   g0[i] = {n_x, n_y, n_z, depth}   unit world normal, distance along the ray
  *   g1[i] = {mv_x, mv_y, roughness, albedo}
- * mv is the previous minus the current screen position in pixels; roughness
- * < 0 marks a Lambertian surface, else GGX with alpha = roughness^2. */
+ * mv is the previous minus the current screen position in pixels. The
+ * roughness slot codes the material: >= 0 GGX with alpha = roughness^2; in
+ * (-1.5, 0) Lambertian (-1 by convention); <= -1.5, with the configuration's
+ * `transparent` set, transparent (-2 by convention; Lambertian otherwise):
+ * a smooth dielectric of index 1.5 that reflects or refracts the
+ * view direction with its Fresnel reflectance. Guiding is off on transparent
+ * surfaces (Sec. 5); their draws are deltas (strategy 3) that do not train,
+ * their estimate is albedo * L along the chosen direction, and pg_eval and
+ * pg_grad give them no finite f_r, density, loss or gradient (all 0). */
 typedef struct {
     const float *g0;
     const float *g1;

@@ -46,7 +46,7 @@ class Config(C.Structure):
                 ("depth_tol", C.c_double), ("normal_tol", C.c_double),
                 ("rough_min", C.c_double), ("sigma2_min", C.c_double), ("rho_max", C.c_double),
                 ("init_mu", C.c_double * 2), ("init_sigma", C.c_double * 3),
-                ("reuse_radius", C.c_int32), ("ggx_f0", C.c_double)]
+                ("reuse_radius", C.c_int32), ("ggx_f0", C.c_double), ("transparent", C.c_int32)]
 
 
 class Camera(C.Structure):
@@ -139,7 +139,7 @@ def _f32(a, shape=None):
 def make_config(width, height, spp=1, seed=0, k_max=32, pi_min=0.05, pi_max=0.95,
                 pi_reinit=0.05, depth_tol=0.1, normal_tol=0.9, rough_min=0.1,
                 sigma2_min=1e-4, rho_max=0.9, init_mu=(0.5, 0.5),
-                init_sigma=(0.1, 0.1, 0.0), reuse_radius=0, ggx_f0=1.0) -> Config:
+                init_sigma=(0.1, 0.1, 0.0), reuse_radius=0, ggx_f0=1.0, transparent=0) -> Config:
     """Thresholds that the GPU applies in binary32 are rounded to binary32 here
     so that both sides compare against the same number."""
     f32 = lambda v: float(np.float32(v))
@@ -153,6 +153,7 @@ def make_config(width, height, spp=1, seed=0, k_max=32, pi_min=0.05, pi_max=0.95
     c.init_sigma[:] = [f32(v) for v in init_sigma]
     c.reuse_radius = int(reuse_radius)
     c.ggx_f0 = f32(ggx_f0)
+    c.transparent = int(transparent)
     return c
 
 

@@ -43,6 +43,7 @@ typedef struct {
     double init_mu[2], init_sigma[3];
     int32_t reuse_radius;    /* neighbour-VPL reuse window radius R (0: off) */
     double ggx_f0;           /* Schlick reflectance of GGX at normal incidence (1: F = 1) */
+    int32_t transparent;     /* 1: roughness codes <= -1.5 are transparent, 0: Lambertian */
 } or_config;
 
 typedef struct {
@@ -680,6 +681,7 @@ static void pixel_setup(const or_config *cfg, const or_camera *cam, int x, int y
     for (int k = 0; k < 3; ++k) { p->n[k] = g0[4 * i + k]; p->pos[k] = o[k] + depth * d[k]; }
     to_local(p->n, wo, p->wo_l);
     p->rough = g1[4 * i + 2];
+    if (!cfg->transparent && is_transparent(p->rough)) p->rough = -1.0;   /* the code is Lambertian then */
     p->albedo = g1[4 * i + 3];
     p->f0 = cfg->ggx_f0;
     derive_gauss(cfg, gm, p->g5);

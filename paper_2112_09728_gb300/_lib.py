@@ -24,7 +24,8 @@ class pg_config(C.Structure):
                 ("depth_tol", C.c_float), ("normal_tol", C.c_float), ("rough_min", C.c_float),
                 ("sigma2_min", C.c_float), ("rho_max", C.c_float), ("init_mu", C.c_float * 2),
                 ("init_sigma", C.c_float * 3), ("init_pi", C.c_float), ("reuse_radius", C.c_int32),
-                ("stochastic_round", C.c_int32)]
+                ("stochastic_round", C.c_int32), ("ggx_f0", C.c_float),
+                ("transparent", C.c_int32)]
 
 
 class pg_camera(C.Structure):

@@ -137,6 +137,7 @@ void pg_config_default(pg_config* c, int32_t width, int32_t height) {
     c->init_sigma[0] = c->init_sigma[1] = 0.1f;
     c->init_sigma[2] = 0.0f;
     c->init_pi = 0.5f;
+    c->ggx_f0 = 1.0f;
 }
 
 pg_status pg_create(const pg_config* cfg, void* stream, pg_ctx** out) {

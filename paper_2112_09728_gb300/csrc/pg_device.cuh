@@ -20,7 +20,7 @@ constexpr float k4OverPi = 1.27323954473516268615f;
 constexpr int kGLTotal = 4 + 6 + 8;
 
 enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
-enum { ST_BRDF = 0, ST_GUIDE = 1, ST_FALLBACK = 2, ST_INVALID = 4 };
+enum { ST_BRDF = 0, ST_GUIDE = 1, ST_FALLBACK = 2, ST_DELTA = 3, ST_INVALID = 4 };
 
 // Everything a launch needs besides its pointers; passed by value (kernel
 // parameter space), so concurrent contexts never share constant memory.
@@ -48,6 +48,8 @@ struct Params {
     // ((2R+1)^2 - 1) spp, and the stride of the walk through them
     int reuse_r, reuse_c, reuse_stride;
     float reuse_inv_spp, reuse_inv_dw;   // 1/spp and 1/(2R+1), for exact floor divisions of small integers
+    float f0;                            // Schlick reflectance of GGX at normal incidence (1: F = 1)
+    int glass;                           // roughness codes <= -1.5 are transparent (else Lambertian)
     int sr;                              // stochastic rounding of the 16-bit EM stores
     uint32_t sr_frame;                   // frame index of the staged update's rounding bits
 };
@@ -557,10 +559,15 @@ __device__ __forceinline__ float guide_pdf(const Guide& d, float ux, float uy) {
 }
 
 // ---------------------------------------------------------------------------
-// Surface: basis, view direction, material (Eq. 1's f_r).
+// Surface: basis, view direction, material (Eq. 1's f_r). The roughness slot
+// codes the material: >= 0 GGX, in (-1.5, 0) Lambertian, <= -1.5 transparent.
 // Lambert: f_r = albedo / pi, cosine-weighted draws.
 // GGX (Walter et al. 2007): alpha = roughness^2 (>= 1e-4), separable Smith
-// shadowing, Fresnel 1; the draw picks h ~ D(h) cos(theta_h) and reflects w_o.
+// shadowing, Schlick's Fresnel F0 + (1 - F0)(1 - o.h)^5 (F0 = 1: F = 1); the
+// draw picks h ~ D(h) cos(theta_h) and reflects w_o.
+// Transparent (Sec. 5, guiding off): a smooth dielectric of index 1.5 that
+// reflects w_o with its Fresnel reflectance and refracts it otherwise; its
+// draws are deltas, with no finite f_r or density.
 // ---------------------------------------------------------------------------
 struct Surf {
     Basis f;
@@ -569,13 +576,26 @@ struct Surf {
     float a2;       // alpha^2 (GGX)
     float albedo;
     float go;       // GGX: albedo G1(w_o) / (4 cos theta_o), 0 when back-facing
-    bool lambert;
+    int mat;        // MAT_GGX, MAT_LAMBERT or MAT_GLASS
 };
+enum { MAT_GGX = 0, MAT_LAMBERT = 1, MAT_GLASS = 2 };
+
+// Unpolarised Fresnel reflectance of the index-1.5 dielectric for light from
+// outside at cosine ci > 0.
+__device__ __forceinline__ float dielectric_fresnel(float ci) {
+    const float n = 1.5f, ct = sqrtf(1.0f - (1.0f - ci * ci) * (1.0f / (n * n)));
+    const float rs = fdiv(ci - n * ct, ci + n * ct), rp = fdiv(n * ci - ct, n * ci + ct);
+    return 0.5f * (rs * rs + rp * rp);
+}
 
 __device__ __forceinline__ float smith_g1(float a2, float c) {
     return __fdividef(2.0f * c, c + sqrtf(fmaf(1.0f - a2, c * c, a2)));
 }
 
+// GLASS = false compiles the transparent material out (its code is then
+// Lambertian, as without P.glass); the kernels that always support it pass
+// true and honour P.glass at run time.
+template <bool GLASS = true>
 __device__ __forceinline__ Surf make_surf(const Params& P, int x, int y, float4 g0, float4 g1) {
     Surf s;
     float3 o, d;
@@ -596,7 +616,7 @@ __device__ __forceinline__ Surf make_surf(const Params& P, int x, int y, float4 
     s.pos = make_float3(o.x + g0.w * d.x, o.y + g0.w * d.y, o.z + g0.w * d.z);
     s.f = make_basis(make_float3(g0.x, g0.y, g0.z));
     s.wo = to_local(s.f, make_float3(-d.x, -d.y, -d.z));
-    s.lambert = g1.z < 0.0f;
+    s.mat = g1.z >= 0.0f ? MAT_GGX : ((GLASS && P.glass && g1.z <= -1.5f) ? MAT_GLASS : MAT_LAMBERT);
     const float a = fmaxf(g1.z * g1.z, 1e-4f);
     s.a2 = a * a;
     s.albedo = g1.w;
@@ -605,13 +625,14 @@ __device__ __forceinline__ Surf make_surf(const Params& P, int x, int y, float4 
 }
 
 // f_r cos(theta_i) and the BRDF draw's density (per steradian) at local wi.
-__device__ __forceinline__ void brdf_eval(const Surf& s, float3 wi, float& fcos, float& pb) {
-    if (!(wi.z > 0.0f)) {
+// f0: Schlick reflectance of the GGX lobe at normal incidence (1: F = 1).
+__device__ __forceinline__ void brdf_eval(const Surf& s, float3 wi, float& fcos, float& pb, float f0) {
+    if (!(wi.z > 0.0f) || s.mat == MAT_GLASS) {
         fcos = 0.0f;
         pb = 0.0f;
         return;
     }
-    if (s.lambert) {
+    if (s.mat == MAT_LAMBERT) {
         pb = wi.z * kInvPi;
         fcos = s.wo.z > 0.0f ? s.albedo * pb : 0.0f;
         return;
@@ -629,14 +650,36 @@ __device__ __forceinline__ void brdf_eval(const Surf& s, float3 wi, float& fcos,
     const float ihl = rsqrtf(hl2);
     const float nh = h.z * ihl, oh = dot3(s.wo, h) * ihl;
     fcos = D * smith_g1(s.a2, wi.z) * s.go;
+    if (f0 < 1.0f) {
+        const float m = 1.0f - oh, m2 = m * m;
+        fcos *= fmaf(1.0f - f0, m2 * m2 * m, f0);
+    }
     pb = oh > 0.0f ? fdiv(D * nh, 4.0f * oh) : 0.0f;
 }
 
-// BRDF draw from two uniforms; false for a wasted draw (below the horizon).
+// The draw of a transparent surface: reflection when x1 < F, refraction (into
+// the lower hemisphere) otherwise; viewed from below it wastes the draw.
+__device__ __forceinline__ bool glass_sample(const Surf& s, float x1, float3& wi) {
+    const float ci = s.wo.z;
+    if (!(ci > 0.0f)) {
+        wi = make_float3(0.0f, 0.0f, 1.0f);
+        return false;
+    }
+    if (x1 < dielectric_fresnel(ci)) {
+        wi = make_float3(-s.wo.x, -s.wo.y, ci);
+    } else {
+        const float eta = 1.0f / 1.5f, ct = sqrtf(1.0f - eta * eta * (1.0f - ci * ci));
+        wi = make_float3(-eta * s.wo.x, -eta * s.wo.y, -ct);
+    }
+    return true;
+}
+
+// BRDF draw from two uniforms (Lambertian or GGX); false for a wasted draw
+// (below the horizon).
 __device__ __forceinline__ bool brdf_sample(const Surf& s, float x1, float x2, float3& wi) {
     float sn, cs;
     sincos_turn(x2, &sn, &cs);
-    if (s.lambert) {
+    if (s.mat == MAT_LAMBERT) {
         const float r = sqrtf(x1);
         wi = make_float3(r * cs, r * sn, sqrtf(1.0f - x1));
         return true;
@@ -691,8 +734,16 @@ __device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, con
         o.fcos = o.pg = o.pb = o.pmix = o.F = o.mis = 0.0f;
         return;
     }
+    if (o.strat == ST_DELTA) {
+        // the Fresnel weight of the chosen branch cancels its probability
+        o.fcos = o.pg = o.pb = o.pmix = 0.0f;
+        o.ux = o.uy = -1.0f;
+        o.F = s.albedo * o.L;
+        o.mis = 1.0f;
+        return;
+    }
     float fr;
-    brdf_eval(s, o.wl, fr, o.pb);
+    brdf_eval(s, o.wl, fr, o.pb, P.f0);
     o.fcos = o.L * fr;
     if (!have_u) {
         const float2 u = hemi_to_square(o.wl);
@@ -724,7 +775,11 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
     const uint4 r0 = philox4x32_10(make_uint4(pix, frame, si, stream0), P.rk);
     const float zeta = unit24(r0.x);
     bool have_u = false, valid;
-    if (zeta < d.pi_eff) {
+    if (s.mat == MAT_GLASS) {
+        // a transparent surface (always gated): one of its two deltas
+        o.strat = ST_DELTA;
+        valid = glass_sample(s, unit24(r0.y), o.wl);
+    } else if (zeta < d.pi_eff) {
         const float x1 = unit24_open0(r0.y), x2 = unit24(r0.z);
         const float rr = sqrtf(-2.0f * __logf(x1));
         float sn, cs;
@@ -822,11 +877,11 @@ struct Stats {
     // It enters with the importance weight f / pb_src and this pixel's
     // posterior, the own samples of the reuse path included.
     __device__ __forceinline__ void add_vpl(const Guide& d, const Gam& g, const Surf& s, float3 ww, float L,
-                                            float pb_src) {
+                                            float pb_src, float f0) {
         const float3 wl = to_local(s.f, ww);
         if (!(wl.z > 0.0f) || !(pb_src > 0.0f)) return;
         float fr, pb;
-        brdf_eval(s, wl, fr, pb);
+        brdf_eval(s, wl, fr, pb, f0);
         const float2 u = hemi_to_square(wl);
         const float pg = guide_pdf(d, u.x, u.y);
         const float pmix = d.pi_eff * pg + (1.0f - d.pi_eff * d.Z) * pb;

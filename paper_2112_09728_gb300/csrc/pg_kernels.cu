@@ -24,8 +24,9 @@ __device__ __forceinline__ bool same_normal(float4 a, float4 b) {
 }
 
 __device__ __forceinline__ bool gated(const Params& P, bool reinit, float4 g1) {
-    // guiding is off for fresh history (Sec. 3.1) and near-mirror GGX (Sec. 5)
-    return reinit || (g1.z >= 0.0f && g1.z < P.rough_min);
+    // guiding is off for fresh history (Sec. 3.1), near-mirror GGX and
+    // transparent surfaces (Sec. 5)
+    return reinit || (g1.z >= 0.0f && g1.z < P.rough_min) || (P.glass && g1.z <= -1.5f);
 }
 
 template <int DT>
@@ -56,8 +57,10 @@ __device__ __forceinline__ bool reproject_pixel(const Params& P, int x, int y, f
 }
 
 // ONE: one sample per pixel, known at compile time (no sample loop, no Kahan
-// compensation state).
-template <int DT, bool ONE>
+// compensation state). GLASS: the transparent material compiled in (launched
+// when the configuration enables it; without it the kernel carries none of
+// its code).
+template <int DT, bool ONE, bool GLASS>
 __global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void* __restrict__ gin,
                                                      void* __restrict__ gout, const float4* __restrict__ g0,
                                                      const float4* __restrict__ g1, const float4* __restrict__ g0p,
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void*
     const float4 a0 = __ldcs(g0 + i), a1 = __ldcs(g1 + i);
     Gam g;
     const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g);
-    const Surf s = make_surf(P, x, y, a0, a1);
+    const Surf s = make_surf<GLASS>(P, x, y, a0, a1);
     const Guide d = derive_guide(P, g, gated(P, reinit, a1));
     Stats st;
     Kahan f;
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
         }
         if (!(pb > 0.0f)) break;
         const float4 v = vpl[q];
-        st.add_vpl(d, g, s, make_float3(v.x, v.y, v.z), v.w, pb);
+        st.add_vpl(d, g, s, make_float3(v.x, v.y, v.z), v.w, pb, P.f0);
     }
     m_step(P, g, st);
     if (!gam_finite(g)) atomicOr(err, 1);
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(kBlock) k_update(const Params P, const float4*
         if (o.strat != ST_BRDF) continue;
         o.wl = to_local(s.f, make_float3(in.wx[q], in.wy[q], in.wz[q]));
         float fr;
-        brdf_eval(s, o.wl, fr, o.pb);
+        brdf_eval(s, o.wl, fr, o.pb, P.f0);
         if (!(o.pb > 0.0f)) continue;
         o.fcos = in.radiance[q] * fr;
         const float2 u = hemi_to_square(o.wl);
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(kBlock) k_eval(const Params P, const void* __r
         const float3 wl = to_local(s.f, ww);
         const float L = radiance(P, s.pos, ww);
         float fr, pb, pg = 0.0f;
-        brdf_eval(s, wl, fr, pb);
+        brdf_eval(s, wl, fr, pb, P.f0);
         if (wl.z > 0.0f) {
             const float2 u = hemi_to_square(wl);
             pg = guide_pdf(d, u.x, u.y);
@@ -515,10 +518,15 @@ cudaError_t launch_init(int dt, const Params& P, void* gam, float init_pi, cudaS
 cudaError_t launch_frame(int dt, const Params& P, const void* gin, void* gout, const float4* g0,
                          const float4* g1, const float4* g0p, float* img, uint32_t frame, int* err,
                          cudaStream_t st) {
-    if (P.spp == 1) {
-        PG_DISPATCH(dt, (k_frame<D, true><<<grid_for(P), kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
+    const dim3 grid = grid_for(P);
+    if (P.spp == 1 && !P.glass) {
+        PG_DISPATCH(dt, (k_frame<D, true, false><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
+    } else if (P.spp == 1) {
+        PG_DISPATCH(dt, (k_frame<D, true, true><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
+    } else if (!P.glass) {
+        PG_DISPATCH(dt, (k_frame<D, false, false><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
     } else {
-        PG_DISPATCH(dt, (k_frame<D, false><<<grid_for(P), kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
+        PG_DISPATCH(dt, (k_frame<D, false, true><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
     }
     return cudaGetLastError();
 }

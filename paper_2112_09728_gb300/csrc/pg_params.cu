@@ -79,6 +79,8 @@ pg_status check_config(const pg_config* c, std::string& why) {
     if (c->reuse_radius < 0 || c->reuse_radius > 8) { why = "reuse_radius outside [0, 8]"; return PG_ERR_ARG; }
     if (c->reuse_radius > 0 && c->k_max < 1) { why = "neighbour reuse needs k_max >= 1"; return PG_ERR_ARG; }
     if (c->stochastic_round != 0 && c->stochastic_round != 1) { why = "stochastic_round must be 0 or 1"; return PG_ERR_ARG; }
+    if (!(c->ggx_f0 >= 0.0f && c->ggx_f0 <= 1.0f)) { why = "ggx_f0 outside [0, 1]"; return PG_ERR_ARG; }
+    if (c->transparent != 0 && c->transparent != 1) { why = "transparent must be 0 or 1"; return PG_ERR_ARG; }
     return PG_OK;
 }
 
@@ -117,6 +119,8 @@ void config_params(const pg_config& cfg, Params& P) {
     // neighbour reuse: C candidates, walked with the smallest stride >= 0.618 C
     // that is coprime with C (so N <= C picks are distinct)
     P.sr = cfg.stochastic_round;
+    P.f0 = cfg.ggx_f0;
+    P.glass = cfg.transparent;
     P.reuse_r = cfg.reuse_radius;
     if (cfg.reuse_radius > 0) {
         const int d = 2 * cfg.reuse_radius + 1;

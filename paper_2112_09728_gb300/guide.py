@@ -77,7 +77,7 @@ def make_config(width, height, spp=1, gamma_dtype="f32", seed=0, **overrides) ->
     for k, v in overrides.items():
         if k in ("init_mu", "init_sigma"):
             getattr(cfg, k)[:] = [float(x) for x in v]
-        elif k in ("k_max", "reuse_radius", "stochastic_round"):
+        elif k in ("k_max", "reuse_radius", "stochastic_round", "transparent"):
             setattr(cfg, k, int(v))
         else:
             setattr(cfg, k, float(v))

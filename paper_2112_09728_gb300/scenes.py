@@ -63,6 +63,7 @@ class Params:
     init_pi: float = 0.5
     reuse_radius: int = 0      # neighbour-VPL reuse window radius (0: off)
     ggx_f0: float = 1.0        # Schlick reflectance of GGX at normal incidence (1: no Fresnel)
+    transparent: int = 0       # 1: roughness codes <= -1.5 are transparent (else Lambertian)
 
 
 def unit_hemisphere_dirs(rng, n, zmin=0.0):
@@ -257,7 +258,9 @@ def random_normals(rng, n, max_tilt=0.6):
     return (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
 
 
-def random_gbuffer(rng, width, height, ggx_frac=0.5, rough_lo=0.02, max_tilt=0.6):
+def random_gbuffer(rng, width, height, ggx_frac=0.5, rough_lo=0.02, max_tilt=0.6, glass_frac=0.0):
+    """Random normals, depths and materials; a share glass_frac of the pixels
+    is transparent (roughness code -2), drawn after the others."""
     hw = width * height
     g0 = np.empty((hw, 4), np.float32)
     g0[:, :3] = random_normals(rng, hw, max_tilt)
@@ -267,6 +270,8 @@ def random_gbuffer(rng, width, height, ggx_frac=0.5, rough_lo=0.02, max_tilt=0.6
     ggx = rng.random(hw) < ggx_frac
     g1[:, 2] = np.where(ggx, rng.uniform(rough_lo, 1.0, hw), -1.0)
     g1[:, 3] = rng.uniform(0.2, 1.0, hw)
+    if glass_frac > 0.0:
+        g1[rng.random(hw) < glass_frac, 2] = -2.0
     return g0, g1
 
 

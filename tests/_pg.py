@@ -10,7 +10,7 @@ def ocfg(par, **kw):
              pi_min=par.pi_min, pi_max=par.pi_max, pi_reinit=par.pi_reinit, depth_tol=par.depth_tol,
              normal_tol=par.normal_tol, rough_min=par.rough_min, sigma2_min=par.sigma2_min,
              rho_max=par.rho_max, init_mu=par.init_mu, init_sigma=par.init_sigma,
-             reuse_radius=par.reuse_radius, ggx_f0=par.ggx_f0)
+             reuse_radius=par.reuse_radius, ggx_f0=par.ggx_f0, transparent=par.transparent)
     d.update(kw)
     return O.make_config(**d)
 
@@ -43,7 +43,7 @@ def guide(par, gamma_dtype="f32"):
                      depth_tol=par.depth_tol, normal_tol=par.normal_tol, rough_min=par.rough_min,
                      sigma2_min=par.sigma2_min, rho_max=par.rho_max, init_mu=par.init_mu,
                      init_sigma=par.init_sigma, init_pi=par.init_pi, reuse_radius=par.reuse_radius,
-                     ggx_f0=par.ggx_f0)
+                     ggx_f0=par.ggx_f0, transparent=par.transparent)
 
 
 def set_gamma_rows(gp, rows):

@@ -79,7 +79,7 @@ def _glass(W, H, albedo=0.7):
 def test_transparent_pixel_under_constant_field_is_exact_and_never_trains():
     W, H = 8, 6
     g0, g1 = _glass(W, H)
-    cfg = O.make_config(W, H, spp=3, seed=9)
+    cfg = O.make_config(W, H, spp=3, seed=9, transparent=1)
     cam = ocam(scenes.top_down_camera(pixel_size=0.2))
     fld = O.make_field(np.zeros((0, 3)), np.zeros(0), np.zeros(0), 0.6)
     rng = np.random.default_rng(0)
@@ -93,12 +93,19 @@ def test_transparent_pixel_under_constant_field_is_exact_and_never_trains():
     assert np.allclose(s["estimate"], a32 * 0.6, rtol=1e-14, atol=0)
     assert np.allclose(img, a32 * 0.6, rtol=1e-14, atol=0)
     assert np.array_equal(out, gam)         # no BRDF-strategy samples: the guide is kept
+    # without the transparent material enabled the code is Lambertian
+    g1l = g1.copy()
+    g1l[:, 2] = -1.0
+    off = O.make_config(W, H, spp=3, seed=9)
+    a = O.frame(off, cam, fld, 2, g0, g1, g0, gam)
+    b = O.frame(off, cam, fld, 2, g0, g1l, g0, gam)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[3], b[3])
 
 
 def test_transparent_pixel_mean_is_the_fresnel_mix_of_its_two_deltas():
     W, H, frames = 16, 16, 40
     g0, g1 = _glass(W, H, albedo=0.9)
-    cfg = O.make_config(W, H, spp=2, seed=21)
+    cfg = O.make_config(W, H, spp=2, seed=21, transparent=1)
     cam = scenes.top_down_camera(pixel_size=0.2)
     d = np.array([[0.3, 0.2, -0.93]])
     d /= np.linalg.norm(d)                  # a lobe below the surface: seen through the glass
