@@ -143,7 +143,14 @@ typedef struct {
  * (normalised on the sphere), times the occlusion mask
  * 0.5 + 0.5 sin(2 pi (mask[0] x + mask[2] w_x)) cos(2 pi (mask[1] y + mask[2] w_y))
  * when mask_kind = 1 (x, y: world position of the shading point), plus
- * constant. */
+ * constant.
+ * With rgb = 1 the field is coloured: lobe j carries amp_rgb[j] and the
+ * constant is constant_rgb (amp and constant are ignored). The pass then
+ * weighs its EM samples by the luminance of the radiance (Sec. 3.1),
+ * Y = 0.2126 R + 0.7152 G + 0.0722 B (Rec. 709): sampling, densities, MIS
+ * and training see the field's luminance, and the per-pixel estimates
+ * written to d_img become three planes [3][H*W] (R, G, B). Per-sample
+ * records (pg_samples) and pg_eval report the luminance. */
 typedef struct {
     int32_t n_lobes;         /* 0..8 */
     float dir[8][3];
@@ -152,6 +159,9 @@ typedef struct {
     float constant;
     int32_t mask_kind;       /* 0 none, 1 sinusoidal mask */
     float mask[4];
+    int32_t rgb;             /* 0 monochrome, 1 coloured (amp_rgb, constant_rgb) */
+    float amp_rgb[8][3];
+    float constant_rgb[3];
 } pg_field;
 
 /* Per-sample record of the path-tracing pass, the counterpart of the paper's
@@ -231,7 +241,8 @@ pg_status pg_frame(pg_ctx *ctx, const pg_gbuffer *cur, const float *d_g0_prev,
  * (t < n_frames, frame index frame0 + t) reads h_g0 + t*H*W*4 and
  * h_g1 + t*H*W*4 (float4 per pixel, as in pg_gbuffer) with cameras[t], its
  * previous g0 being frame t-1's (for t = 0: h_g0_prev, or its own g0 when
- * NULL), and writes its per-pixel estimate to h_img + t*H*W (nullable). The
+ * NULL), and writes its per-pixel estimate to h_img + t*H*W (nullable; with a
+ * coloured field three planes, at h_img + t*3*H*W). The
  * uploads, the frames and the read-backs run on three streams so that
  * neighbouring frames overlap; device rings of three g0, two g1 and two image
  * buffers are reused only after the frames that read them have finished.

@@ -58,7 +58,8 @@ class Camera(C.Structure):
 class Field(C.Structure):
     _fields_ = [("n_lobes", C.c_int32), ("dir", (C.c_double * 3) * 8),
                 ("kappa", C.c_double * 8), ("amp", C.c_double * 8), ("constant", C.c_double),
-                ("mask_kind", C.c_int32), ("mask", C.c_double * 4)]
+                ("mask_kind", C.c_int32), ("mask", C.c_double * 4), ("rgb", C.c_int32),
+                ("amp_rgb", (C.c_double * 3) * 8), ("constant_rgb", C.c_double * 3)]
 
 
 class Samples(C.Structure):
@@ -166,7 +167,8 @@ def make_camera(kind, origin, fwd, right, up, pixel_size=1.0, tan_half_fov=0.0) 
     return c
 
 
-def make_field(dirs, kappas, amps, constant=0.0, mask=None) -> Field:
+def make_field(dirs, kappas, amps, constant=0.0, mask=None, rgb=None, constant_rgb=None) -> Field:
+    """rgb: [n, 3] lobe colours (a coloured field; amps then unused)."""
     f = Field()
     n = len(kappas)
     assert n <= 8
@@ -175,6 +177,11 @@ def make_field(dirs, kappas, amps, constant=0.0, mask=None) -> Field:
         f.dir[j][:] = [float(v) for v in dirs[j]]
         f.kappa[j], f.amp[j] = float(kappas[j]), float(amps[j])
     f.constant = float(constant)
+    if rgb is not None:
+        f.rgb = 1
+        for j in range(n):
+            f.amp_rgb[j][:] = [float(v) for v in rgb[j]]
+        f.constant_rgb[:] = [float(v) for v in (constant_rgb if constant_rgb is not None else (0.0, 0.0, 0.0))]
     if mask is None:
         f.mask_kind = 0
     else:
@@ -317,13 +324,14 @@ def _alloc_samples(n):
 
 
 def sample(cfg, cam, field, frame, g0, g1, gam, reinit=None):
-    """Sampling step. Returns (samples dict of [spp*HW] arrays, img [HW])."""
+    """Sampling step. Returns (samples dict of [spp*HW] arrays, img [HW], or
+    [3*HW] planes R, G, B for a coloured field)."""
     hw = cfg.width * cfg.height
     g0, g1 = _f32(g0, (hw, 4)), _f32(g1, (hw, 4))
     gam = _f64(gam, (hw, 8))
     rein = None if reinit is None else np.ascontiguousarray(reinit, np.uint8).reshape(hw)
     s, arrs = _alloc_samples(cfg.spp * hw)
-    img = np.empty(hw)
+    img = np.empty((3 if field.rgb else 1) * hw)
     _load().or_sample(C.byref(cfg), C.byref(cam), C.byref(field), int(frame) & 0xFFFFFFFF,
                       _ptr(g0), _ptr(g1), _ptr(gam), _ptr(rein), C.byref(s), _ptr(img))
     return arrs, img
@@ -355,14 +363,15 @@ def reuse_picks(cfg, k, pix, frame_idx):
 
 
 def frame(cfg, cam, field, frame_idx, g0, g1, g0_prev, gam_prev):
-    """One fused frame. Returns (gamma_out, accept, samples dict, img)."""
+    """One fused frame. Returns (gamma_out, accept, samples dict, img); img is
+    [3*HW] (planes R, G, B) for a coloured field."""
     hw = cfg.width * cfg.height
     g0, g1, g0p = _f32(g0, (hw, 4)), _f32(g1, (hw, 4)), _f32(g0_prev, (hw, 4))
     gp = _f64(gam_prev, (hw, 8))
     out = np.empty((hw, 8))
     acc = np.empty(hw, np.uint8)
     s, arrs = _alloc_samples(cfg.spp * hw)
-    img = np.empty(hw)
+    img = np.empty((3 if field.rgb else 1) * hw)
     _load().or_frame(C.byref(cfg), C.byref(cam), C.byref(field), int(frame_idx) & 0xFFFFFFFF,
                      _ptr(g0), _ptr(g1), _ptr(g0p), _ptr(gp), _ptr(out), _ptr(acc), C.byref(s),
                      _ptr(img))

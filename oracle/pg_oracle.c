@@ -59,6 +59,9 @@ typedef struct {
     double constant;
     int32_t mask_kind;       /* 0 none, 1 sinusoidal occlusion mask */
     double mask[4];          /* f1, f2, g, unused */
+    int32_t rgb;             /* 1: coloured lobes amp_rgb and constant constant_rgb */
+    double amp_rgb[8][3];
+    double constant_rgb[3];
 } or_field;
 
 /* Per-sample outputs of the sampling step, sample-major [s*HW + i]. */
@@ -465,8 +468,33 @@ int or_brdf_sample(double rough, const double wo[3], double x1, double x2, doubl
 /* optionally times a smooth occlusion mask of the world position and the   */
 /* direction, plus a constant.                                              */
 /* ------------------------------------------------------------------------ */
+/* The coloured field's channels (a monochrome field gives its value in all three). */
+void or_radiance_rgb(const or_field *f, const double x[3], const double w[3], double out[3])
+{
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < f->n_lobes; ++j) {
+        double k = f->kappa[j];
+        double dot = f->dir[j][0] * w[0] + f->dir[j][1] * w[1] + f->dir[j][2] * w[2];
+        double v = k / (2.0 * M_PI * (1.0 - exp(-2.0 * k))) * exp(k * (dot - 1.0));
+        for (int c = 0; c < 3; ++c) s[c] += (f->rgb ? f->amp_rgb[j][c] : f->amp[j]) * v;
+    }
+    double m = 1.0;
+    if (f->mask_kind == 1)
+        m = 0.5 + 0.5 * sin(2.0 * M_PI * (f->mask[0] * x[0] + f->mask[2] * w[0])) *
+                  cos(2.0 * M_PI * (f->mask[1] * x[1] + f->mask[2] * w[1]));
+    for (int c = 0; c < 3; ++c) out[c] = s[c] * m + (f->rgb ? f->constant_rgb[c] : f->constant);
+}
+
+/* The radiance the pass works with: the field's value, or for a coloured
+ * field its luminance (Sec. 3.1 weighs by the radiance's luminance), with the
+ * Rec. 709 weights Y = 0.2126 R + 0.7152 G + 0.0722 B. */
 double or_radiance(const or_field *f, const double x[3], const double w[3])
 {
+    if (f->rgb) {
+        double c[3];
+        or_radiance_rgb(f, x, w, c);
+        return 0.2126 * c[0] + 0.7152 * c[1] + 0.0722 * c[2];
+    }
     double s = 0.0;
     for (int j = 0; j < f->n_lobes; ++j) {
         double k = f->kappa[j];
@@ -776,13 +804,14 @@ static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_fi
     pixel_ctx p;
     pixel_setup(cfg, cam, x, y, g0, g1, gm, reinit, &p);
     uint32_t key[2] = {cfg->seed_lo, cfg->seed_hi};
-    double sum = 0.0;
+    double sum = 0.0, sum_rgb[3] = {0.0, 0.0, 0.0};
     for (int s = 0; s < spp; ++s) {
         int64_t o = (int64_t)s * HW + i;
         double wl[3], u[2], margin;
         int valid, have_u;
         int strat = draw_direction(&p, key, (uint32_t)i, frame, (uint32_t)s, 0u, wl, u, &have_u, &valid,
                                    &margin);
+        double wgt = 0.0;   /* the estimate per unit radiance, for the colour channels */
         double fcos = 0, pg = 0, pb = 0, pmix = 0, rad, uo[2] = {-1.0, -1.0};
         double F = 0.0, mis = 0.0;
         if (valid && strat == S_DELTA) {
@@ -792,11 +821,13 @@ static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_fi
             to_world(p.n, wl, wwi);
             rad = or_radiance(fld, p.pos, wwi);
             F = p.albedo * rad;
+            wgt = p.albedo;
             mis = 1.0;
         } else if (valid) {
             eval_local(fld, &p, wl, have_u ? u : NULL, &fcos, &pg, &pb, &pmix, &rad, uo);
             if (pmix > 0.0) {
                 F = fcos / pmix;
+                wgt = (wl[2] > 0.0 ? or_brdf_cos_f0(p.rough, p.albedo, p.f0, p.wo_l, wl) : 0.0) / pmix;
                 mis = strat == S_GUIDE ? p.pi_eff * pg / pmix : (1.0 - p.pi_eff * p.Z) * pb / pmix;
             }
         } else {
@@ -818,8 +849,17 @@ static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_fi
         if (S->ux) { S->ux[o] = uo[0]; S->uy[o] = uo[1]; }
         if (S->margin) S->margin[o] = margin;
         sum += F;
+        if (fld->rgb) {
+            double c[3];
+            or_radiance_rgb(fld, p.pos, ww, c);
+            for (int k = 0; k < 3; ++k) sum_rgb[k] += wgt * c[k];
+        }
     }
-    img[i] = sum / spp;
+    if (fld->rgb) {
+        for (int k = 0; k < 3; ++k) img[k * HW + i] = sum_rgb[k] / spp;
+    } else {
+        img[i] = sum / spp;
+    }
 }
 
 void or_sample(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,

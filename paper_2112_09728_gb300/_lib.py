@@ -41,7 +41,8 @@ class pg_gbuffer(C.Structure):
 class pg_field(C.Structure):
     _fields_ = [("n_lobes", C.c_int32), ("dir", (C.c_float * 3) * 8), ("kappa", C.c_float * 8),
                 ("amp", C.c_float * 8), ("constant", C.c_float), ("mask_kind", C.c_int32),
-                ("mask", C.c_float * 4)]
+                ("mask", C.c_float * 4), ("rgb", C.c_int32), ("amp_rgb", (C.c_float * 3) * 8),
+                ("constant_rgb", C.c_float * 3)]
 
 
 class pg_samples(C.Structure):

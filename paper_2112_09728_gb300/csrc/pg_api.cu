@@ -90,7 +90,7 @@ pg_status ensure_host(pg_ctx* c) {
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaMalloc(&c->hg0[k], hw * sizeof(float4));
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         e = cudaMalloc(&c->hg1[k], hw * sizeof(float4));
-        if (e == cudaSuccess) e = cudaMalloc(&c->himg[k], hw * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&c->himg[k], 3 * hw * sizeof(float));   // room for three planes
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -289,8 +289,8 @@ pg_status pg_frame(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, con
     pg_status s = check_gbuffer(c, cur);
     if (s != PG_OK) return s;
     if (!d_g0_prev || !aligned16(d_g0_prev)) return fail(c, PG_ERR_ARG, "d_g0_prev NULL or not 16-byte aligned");
-    const size_t hw = hw_of(c);
-    if (overlaps(d_img, hw * 4, c->gam[0], c->gam_bytes) || overlaps(d_img, hw * 4, c->gam[1], c->gam_bytes))
+    const size_t ib = hw_of(c) * 4 * (field && field->rgb ? 3 : 1);
+    if (overlaps(d_img, ib, c->gam[0], c->gam_bytes) || overlaps(d_img, ib, c->gam[1], c->gam_bytes))
         return fail(c, PG_ERR_ARG, "d_img overlaps Gamma");
     return frame_impl(c, cur, d_g0_prev, field, frame, d_img);
 }
@@ -302,9 +302,11 @@ pg_status pg_frames_host(pg_ctx* c, int32_t n_frames, const float* h_g0, const f
     if (c->phase != 0) return fail(c, PG_ERR_STATE, "pg_frames_host: a staged frame is in progress");
     if (n_frames < 1 || n_frames > (1 << 20)) return fail(c, PG_ERR_ARG, "pg_frames_host: n_frames outside [1, 2^20]");
     if (!h_g0 || !h_g1 || !cameras) return fail(c, PG_ERR_ARG, "pg_frames_host: h_g0, h_g1 and cameras are required");
+    if (!field) return fail(c, PG_ERR_ARG, "pg_frames_host: field is NULL");
     pg_status s = ensure_host(c);
     if (s != PG_OK) return s;
-    const size_t hw = hw_of(c), gbytes = hw * sizeof(float4), ibytes = hw * sizeof(float);
+    const size_t planes = field->rgb ? 3 : 1;
+    const size_t hw = hw_of(c), gbytes = hw * sizeof(float4), ibytes = planes * hw * sizeof(float);
     cudaError_t e = cudaSuccess;
     // step t: upload into g0 slot t % 3 and g1 slot t % 2, once step t-2 (the
     // last reader of both slots) has run; run once the upload is in and step
@@ -338,7 +340,8 @@ pg_status pg_frames_host(pg_ctx* c, int32_t n_frames, const float* h_g0, const f
         if (e == cudaSuccess && h_img) {
             e = cudaStreamWaitEvent(c->hs_down, c->ev_ran[k], 0);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(h_img + (size_t)t * hw, c->himg[b], ibytes, cudaMemcpyDeviceToHost, c->hs_down);
+                e = cudaMemcpyAsync(h_img + (size_t)t * planes * hw, c->himg[b], ibytes, cudaMemcpyDeviceToHost,
+                                    c->hs_down);
             if (e == cudaSuccess) e = cudaEventRecord(c->ev_down[k], c->hs_down);
         }
     }

@@ -41,6 +41,10 @@ struct Params {
     float lobe_dir[8][3], lobe_kappa[8], lobe_scale[8];  // scale = amp * vMF normaliser
     float lobe_e2[8];                                     // -kappa log2(e) / 2: exponent per |w - d|^2 in base 2
     float field_const, mask[3];
+    // coloured field: per-lobe scale of each channel and the constant's
+    // channels (lobe_scale and field_const then hold the luminance)
+    int rgb;
+    float lobe_rgb[8][3], field_const_rgb[3];
     // Gauss-Legendre rules on [-1, 1] with 4, 6 and 8 nodes, back to back
     // (computed on the host at context creation)
     float gl_x[kGLTotal], gl_w[kGLTotal];
@@ -697,20 +701,35 @@ __device__ __forceinline__ bool brdf_sample(const Surf& s, float x1, float x2, f
 // Each lobe is amp * C_k exp(-k |w - d|^2 / 2) (= amp * C_k exp(k (d.w - 1))
 // for unit vectors, in a form that keeps its precision near the peak).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float radiance(const Params& P, float3 pos, float3 w) {
-    float s = 0.0f;
+// Returns the radiance's luminance (the field itself when monochrome); with
+// RGB, *rgb receives its three channels (coloured fields).
+template <bool RGB = false>
+__device__ __forceinline__ float radiance(const Params& P, float3 pos, float3 w, float3* rgb = nullptr) {
+    float s = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         if (j < P.n_lobes) {
             const float dx = w.x - P.lobe_dir[j][0], dy = w.y - P.lobe_dir[j][1], dz = w.z - P.lobe_dir[j][2];
-            s = fmaf(P.lobe_scale[j], exp2_approx(P.lobe_e2[j] * fmaf(dx, dx, fmaf(dy, dy, dz * dz))), s);
+            const float e = exp2_approx(P.lobe_e2[j] * fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            s = fmaf(P.lobe_scale[j], e, s);
+            if (RGB) {
+                sr = fmaf(P.lobe_rgb[j][0], e, sr);
+                sg = fmaf(P.lobe_rgb[j][1], e, sg);
+                sb = fmaf(P.lobe_rgb[j][2], e, sb);
+            }
         }
     }
     if (P.mask_kind == 1) {
         const float m = 0.5f + 0.5f * sinpif(2.0f * (P.mask[0] * pos.x + P.mask[2] * w.x)) *
                                    cospif(2.0f * (P.mask[1] * pos.y + P.mask[2] * w.y));
         s *= m;
+        if (RGB) {
+            sr *= m;
+            sg *= m;
+            sb *= m;
+        }
     }
+    if (RGB) *rgb = make_float3(sr + P.field_const_rgb[0], sg + P.field_const_rgb[1], sb + P.field_const_rgb[2]);
     return s + P.field_const;
 }
 
@@ -722,14 +741,18 @@ __device__ __forceinline__ float radiance(const Params& P, float3 pos, float3 w)
 struct Smp {
     float3 wl;        // local direction
     float ux, uy;     // square coordinate of wl
-    float L, fcos;    // radiance and L f_r cos
+    float L, fcos;    // radiance (luminance) and L f_r cos
     float pg, pb, pmix, F, mis;
     int strat;        // ST_* | ST_INVALID
+    float3 Lrgb;      // coloured fields: the radiance's channels
+    float wgt;        // coloured fields: the estimate per unit radiance (F = wgt L per channel)
 };
 
+template <bool RGB = false>
 __device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, const Surf& s, Smp& o, bool have_u) {
     const float3 ww = to_world(s.f, o.wl);
-    o.L = radiance(P, s.pos, ww);
+    o.L = radiance<RGB>(P, s.pos, ww, &o.Lrgb);
+    o.wgt = 0.0f;
     if (o.strat & ST_INVALID) {
         o.fcos = o.pg = o.pb = o.pmix = o.F = o.mis = 0.0f;
         return;
@@ -739,6 +762,7 @@ __device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, con
         o.fcos = o.pg = o.pb = o.pmix = 0.0f;
         o.ux = o.uy = -1.0f;
         o.F = s.albedo * o.L;
+        o.wgt = s.albedo;
         o.mis = 1.0f;
         return;
     }
@@ -756,6 +780,7 @@ __device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, con
     o.pmix = wg + wb;
     if (o.pmix > 0.0f) {
         o.F = fdiv(o.fcos, o.pmix);
+        if (RGB) o.wgt = fdiv(fr, o.pmix);
         o.mis = fdiv((o.strat & 3) == ST_GUIDE ? wg : wb, o.pmix);
     } else {
         o.F = 0.0f;
@@ -769,6 +794,7 @@ __device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, con
 // drive Box-Muller for a guide draw or the BRDF draw otherwise (independent
 // of word 0, hence still uniform given the choice); a guide draw that left
 // the square takes its BRDF draw from word 3 and the low bytes of words 0-2.
+template <bool RGB = false>
 __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, const Surf& s, uint32_t pix,
                                            uint32_t frame, uint32_t si, uint32_t stream0 = 0u) {
     Smp o;
@@ -804,7 +830,7 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
         valid = brdf_sample(s, unit24(r0.y), unit24(r0.z), o.wl);
     }
     if (!valid) o.strat |= ST_INVALID;
-    eval_sample(P, d, s, o, have_u);
+    eval_sample<RGB>(P, d, s, o, have_u);
     return o;
 }
 

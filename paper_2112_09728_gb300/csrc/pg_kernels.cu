@@ -60,7 +60,8 @@ __device__ __forceinline__ bool reproject_pixel(const Params& P, int x, int y, f
 // compensation state). GLASS: the transparent material compiled in (launched
 // when the configuration enables it; without it the kernel carries none of
 // its code).
-template <int DT, bool ONE, bool GLASS>
+// RGB: a coloured field; the image gets three planes [3][H*W].
+template <int DT, bool ONE, bool GLASS, bool RGB>
 __global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void* __restrict__ gin,
                                                      void* __restrict__ gout, const float4* __restrict__ g0,
                                                      const float4* __restrict__ g1, const float4* __restrict__ g0p,
@@ -75,17 +76,39 @@ __global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void*
     const Surf s = make_surf<GLASS>(P, x, y, a0, a1);
     const Guide d = derive_guide(P, g, gated(P, reinit, a1));
     Stats st;
-    Kahan f;
+    Kahan f, fr, fg, fb;
     const int spp = ONE ? 1 : P.spp;
     for (int si = 0; si < spp; ++si) {
-        const Smp o = draw_sample(P, d, s, (uint32_t)i, frame, (uint32_t)si);
-        if (si == 0) f.set(o.F); else f.add(o.F);
+        const Smp o = draw_sample<RGB>(P, d, s, (uint32_t)i, frame, (uint32_t)si);
+        if (si == 0) {
+            f.set(o.F);
+            if (RGB) {
+                fr.set(o.wgt * o.Lrgb.x);
+                fg.set(o.wgt * o.Lrgb.y);
+                fb.set(o.wgt * o.Lrgb.z);
+            }
+        } else {
+            f.add(o.F);
+            if (RGB) {
+                fr.add(o.wgt * o.Lrgb.x);
+                fg.add(o.wgt * o.Lrgb.y);
+                fb.add(o.wgt * o.Lrgb.z);
+            }
+        }
         st.add_train(d, g, o);
     }
     m_step(P, g, st);
     if (!gam_finite(g)) atomicOr(err, 1);
     store_step<DT>(P, gout, hw, (size_t)i, g, frame);
-    if (img) __stcs(img + i, ONE ? f.s : fdiv(f.s, (float)spp));
+    if (img) {
+        if (RGB) {
+            __stcs(img + i, ONE ? fr.s : fdiv(fr.s, (float)spp));
+            __stcs(img + hw + i, ONE ? fg.s : fdiv(fg.s, (float)spp));
+            __stcs(img + 2 * hw + i, ONE ? fb.s : fdiv(fb.s, (float)spp));
+        } else {
+            __stcs(img + i, ONE ? f.s : fdiv(f.s, (float)spp));
+        }
+    }
 }
 
 // Neighbour-VPL reuse, pass 1 (path tracing, Fig. 2): the frame's samples
@@ -93,7 +116,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void*
 // direction and radiance in vpl, and in pb_src the density of the pixel's
 // BRDF draw for a BRDF-strategy sample (0 for samples that do not train).
 // The guide's rectangle mass Z goes to zbuf for the training pass.
-template <int DT, bool ONE>
+template <int DT, bool ONE, bool RGB>
 __global__ void __launch_bounds__(kBlock, 5) k_pt(const Params P, const void* __restrict__ gin,
                                                   const float4* __restrict__ g0, const float4* __restrict__ g1,
                                                   const float4* __restrict__ g0p, float* __restrict__ img,
@@ -109,17 +132,39 @@ __global__ void __launch_bounds__(kBlock, 5) k_pt(const Params P, const void* __
     const Surf s = make_surf(P, x, y, a0, a1);
     const Guide d = derive_guide(P, g, gated(P, reinit, a1));
     zbuf[i] = d.Z;
-    Kahan f;
+    Kahan f, fr, fg, fb;
     const int spp = ONE ? 1 : P.spp;
     for (int si = 0; si < spp; ++si) {
-        const Smp o = draw_sample(P, d, s, (uint32_t)i, frame, (uint32_t)si);
-        if (si == 0) f.set(o.F); else f.add(o.F);
+        const Smp o = draw_sample<RGB>(P, d, s, (uint32_t)i, frame, (uint32_t)si);
+        if (si == 0) {
+            f.set(o.F);
+            if (RGB) {
+                fr.set(o.wgt * o.Lrgb.x);
+                fg.set(o.wgt * o.Lrgb.y);
+                fb.set(o.wgt * o.Lrgb.z);
+            }
+        } else {
+            f.add(o.F);
+            if (RGB) {
+                fr.add(o.wgt * o.Lrgb.x);
+                fg.add(o.wgt * o.Lrgb.y);
+                fb.add(o.wgt * o.Lrgb.z);
+            }
+        }
         const float3 ww = to_world(s.f, o.wl);
         const size_t q = (size_t)si * hw + i;
         vpl[q] = make_float4(ww.x, ww.y, ww.z, o.L);
         pb_src[q] = (o.strat == ST_BRDF && o.pb > 0.0f) ? o.pb : 0.0f;
     }
-    if (img) __stcs(img + i, ONE ? f.s : fdiv(f.s, (float)spp));
+    if (img) {
+        if (RGB) {
+            __stcs(img + i, ONE ? fr.s : fdiv(fr.s, (float)spp));
+            __stcs(img + hw + i, ONE ? fg.s : fdiv(fg.s, (float)spp));
+            __stcs(img + 2 * hw + i, ONE ? fb.s : fdiv(fb.s, (float)spp));
+        } else {
+            __stcs(img + i, ONE ? f.s : fdiv(f.s, (float)spp));
+        }
+    }
 }
 
 // Neighbour-VPL reuse, pass 2 (training, Sec. 3.2 and 4.2): the pixel's own
@@ -224,10 +269,13 @@ __global__ void __launch_bounds__(kBlock) k_sample(const Params P, const float4*
     const Gam g = Work<DT>::load(work, hw, (size_t)i);
     const Surf s = make_surf(P, x, y, a0, a1);
     const Guide d = derive_guide(P, g, gated(P, g.k < 0.0f, a1));
-    Kahan f;
+    Kahan f, fr, fg, fb;
     for (int si = 0; si < P.spp; ++si) {
-        const Smp o = draw_sample(P, d, s, (uint32_t)i, frame, (uint32_t)si);
+        const Smp o = draw_sample<true>(P, d, s, (uint32_t)i, frame, (uint32_t)si);
         f.add(o.F);
+        fr.add(o.wgt * o.Lrgb.x);
+        fg.add(o.wgt * o.Lrgb.y);
+        fb.add(o.wgt * o.Lrgb.z);
         const size_t q = (size_t)si * hw + i;
         if (out.wx) {
             const float3 ww = to_world(s.f, o.wl);
@@ -241,7 +289,15 @@ __global__ void __launch_bounds__(kBlock) k_sample(const Params P, const float4*
         if (out.estimate) out.estimate[q] = o.F;
         if (out.strategy) out.strategy[q] = (uint8_t)o.strat;
     }
-    if (img) img[i] = fdiv(f.s, (float)P.spp);
+    if (img) {
+        if (P.rgb) {
+            img[i] = fdiv(fr.s, (float)P.spp);
+            img[hw + i] = fdiv(fg.s, (float)P.spp);
+            img[2 * hw + i] = fdiv(fb.s, (float)P.spp);
+        } else {
+            img[i] = fdiv(f.s, (float)P.spp);
+        }
+    }
 }
 
 // Training pass on given samples (Sec. 3.2): the E-step re-evaluates each
@@ -519,28 +575,39 @@ cudaError_t launch_frame(int dt, const Params& P, const void* gin, void* gout, c
                          const float4* g1, const float4* g0p, float* img, uint32_t frame, int* err,
                          cudaStream_t st) {
     const dim3 grid = grid_for(P);
-    if (P.spp == 1 && !P.glass) {
-        PG_DISPATCH(dt, (k_frame<D, true, false><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
-    } else if (P.spp == 1) {
-        PG_DISPATCH(dt, (k_frame<D, true, true><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
-    } else if (!P.glass) {
-        PG_DISPATCH(dt, (k_frame<D, false, false><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
-    } else {
-        PG_DISPATCH(dt, (k_frame<D, false, true><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)));
+#define PG_FRAME(ONE, GLASS, RGB) \
+    PG_DISPATCH(dt, (k_frame<D, ONE, GLASS, RGB><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)))
+    const int v = (P.spp == 1 ? 4 : 0) + (P.glass ? 2 : 0) + (P.rgb ? 1 : 0);
+    switch (v) {
+        case 0: PG_FRAME(false, false, false); break;
+        case 1: PG_FRAME(false, false, true); break;
+        case 2: PG_FRAME(false, true, false); break;
+        case 3: PG_FRAME(false, true, true); break;
+        case 4: PG_FRAME(true, false, false); break;
+        case 5: PG_FRAME(true, false, true); break;
+        case 6: PG_FRAME(true, true, false); break;
+        default: PG_FRAME(true, true, true); break;
     }
+#undef PG_FRAME
     return cudaGetLastError();
 }
 
 cudaError_t launch_pt(int dt, const Params& P, const void* gin, const float4* g0, const float4* g1,
                       const float4* g0p, float* img, uint32_t frame, float4* vpl, float* pb_src, float* zbuf,
                       cudaStream_t st) {
-    if (P.spp == 1) {
-        PG_DISPATCH(dt, (k_pt<D, true><<<grid_for(P), kBlock, 0, st>>>(P, gin, g0, g1, g0p, img, frame, vpl, pb_src,
-                                                                       zbuf)));
+    const dim3 grid = grid_for(P);
+#define PG_PT(ONE, RGB) \
+    PG_DISPATCH(dt, (k_pt<D, ONE, RGB><<<grid, kBlock, 0, st>>>(P, gin, g0, g1, g0p, img, frame, vpl, pb_src, zbuf)))
+    if (P.spp == 1 && P.rgb) {
+        PG_PT(true, true);
+    } else if (P.spp == 1) {
+        PG_PT(true, false);
+    } else if (P.rgb) {
+        PG_PT(false, true);
     } else {
-        PG_DISPATCH(dt, (k_pt<D, false><<<grid_for(P), kBlock, 0, st>>>(P, gin, g0, g1, g0p, img, frame, vpl, pb_src,
-                                                                        zbuf)));
+        PG_PT(false, false);
     }
+#undef PG_PT
     return cudaGetLastError();
 }
 

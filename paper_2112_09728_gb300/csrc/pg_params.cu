@@ -158,23 +158,31 @@ pg_status field_params(const pg_field* f, Params& P, std::string& why) {
     if (!f) { why = "field is NULL"; return PG_ERR_ARG; }
     if (f->n_lobes < 0 || f->n_lobes > 8) { why = "n_lobes outside [0, 8]"; return PG_ERR_ARG; }
     if (f->mask_kind != 0 && f->mask_kind != 1) { why = "mask_kind must be 0 or 1"; return PG_ERR_ARG; }
+    if (f->rgb != 0 && f->rgb != 1) { why = "rgb must be 0 or 1"; return PG_ERR_ARG; }
+    // Rec. 709 luminance of a colour
+    auto lum = [](const float* c) { return 0.2126 * c[0] + 0.7152 * c[1] + 0.0722 * c[2]; };
     P.n_lobes = f->n_lobes;
+    P.rgb = f->rgb;
     for (int j = 0; j < 8; ++j) {
         for (int k = 0; k < 3; ++k) P.lobe_dir[j][k] = j < f->n_lobes ? f->dir[j][k] : 0.0f;
         if (j < f->n_lobes) {
             const double kap = f->kappa[j];
             if (!(kap > 0.0) || !std::isfinite(kap)) { why = "lobe kappa must be > 0"; return PG_ERR_ARG; }
             // normalised vMF on the sphere: kappa / (2 pi (1 - exp(-2 kappa)))
+            const double norm = kap / (2.0 * M_PI * -std::expm1(-2.0 * kap));
             P.lobe_kappa[j] = (float)kap;
-            P.lobe_scale[j] = (float)((double)f->amp[j] * kap / (2.0 * M_PI * -std::expm1(-2.0 * kap)));
+            P.lobe_scale[j] = (float)((f->rgb ? lum(f->amp_rgb[j]) : (double)f->amp[j]) * norm);
+            for (int c = 0; c < 3; ++c) P.lobe_rgb[j][c] = f->rgb ? (float)((double)f->amp_rgb[j][c] * norm) : 0.0f;
             P.lobe_e2[j] = (float)(-0.5 * kap / std::log(2.0));
         } else {
             P.lobe_kappa[j] = 0.0f;
             P.lobe_scale[j] = 0.0f;
             P.lobe_e2[j] = 0.0f;
+            for (int c = 0; c < 3; ++c) P.lobe_rgb[j][c] = 0.0f;
         }
     }
-    P.field_const = f->constant;
+    P.field_const = f->rgb ? (float)lum(f->constant_rgb) : f->constant;
+    for (int c = 0; c < 3; ++c) P.field_const_rgb[c] = f->rgb ? f->constant_rgb[c] : 0.0f;
     P.mask_kind = f->mask_kind;
     for (int k = 0; k < 3; ++k) P.mask[k] = f->mask[k];
     return PG_OK;

@@ -53,6 +53,11 @@ def make_field(fld) -> L.pg_field:
         f.kappa[j] = float(fld.kappas[j])
         f.amp[j] = float(fld.amps[j])
     f.constant = float(fld.constant)
+    if getattr(fld, "rgb", None) is not None:
+        f.rgb = 1
+        for j in range(n):
+            f.amp_rgb[j][:] = [float(v) for v in fld.rgb[j]]
+        f.constant_rgb[:] = [float(v) for v in (fld.constant_rgb or (0.0, 0.0, 0.0))]
     if fld.mask is None:
         f.mask_kind = 0
     else:
@@ -149,9 +154,14 @@ class GuidePass:
                    C.c_void_p(_ptr(g0_prev, what="g0_prev", align16=True)),
                    C.c_void_p(_ptr(accept, dtype=torch.uint8, what="accept")))
 
+    @staticmethod
+    def image_planes(field):
+        """1, or 3 for a coloured field (R, G, B planes)."""
+        return 3 if getattr(field, "rgb", None) is not None else 1
+
     def pg_sample(self, g0, g1, camera, field, frame, samples=None, img=None):
         if img is not None:
-            self._check_len(img, self.hw, "img")
+            self._check_len(img, self.image_planes(field) * self.hw, "img")
         ps = self._samples(samples)
         self._call("pg_sample", C.byref(self._gbuf(g0, g1, camera)), C.byref(make_field(field)),
                    C.c_uint32(int(frame) & 0xFFFFFFFF), C.byref(ps), C.c_void_p(_ptr(img, what="img")))
@@ -162,7 +172,7 @@ class GuidePass:
     def pg_frame(self, g0, g1, camera, g0_prev, field, frame, img=None):
         self._check_len(g0_prev, 4 * self.hw, "g0_prev")
         if img is not None:
-            self._check_len(img, self.hw, "img")
+            self._check_len(img, self.image_planes(field) * self.hw, "img")
         self._call("pg_frame", C.byref(self._gbuf(g0, g1, camera)),
                    C.c_void_p(_ptr(g0_prev, what="g0_prev", align16=True)), C.byref(make_field(field)),
                    C.c_uint32(int(frame) & 0xFFFFFFFF), C.c_void_p(_ptr(img, what="img")))
@@ -171,7 +181,8 @@ class GuidePass:
         """n whole frames from host memory: g0, g1 CPU float32 tensors [n, H*W, 4]
         (page-locked for overlapped copies), cameras a list of n cameras,
         g0_prev the g0 before frame 0 (CPU [H*W, 4] or None), img a CPU float32
-        tensor [n, H*W] for the estimates (or None). Returns img."""
+        tensor [n, planes * H*W] for the estimates (planes = 3 for a coloured
+        field) or None. Returns img."""
         n = len(cameras)
         for t, what in ((g0, "g0"), (g1, "g1")):
             if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
@@ -184,7 +195,7 @@ class GuidePass:
         if img is not None:
             if img.is_cuda or img.dtype != torch.float32 or not img.is_contiguous():
                 raise TypeError("img must be a contiguous float32 CPU tensor")
-            self._check_len(img, n * self.hw, "img")
+            self._check_len(img, n * self.image_planes(field) * self.hw, "img")
         cams = (L.pg_camera * n)(*[make_camera(c) for c in cameras])
         self._call("pg_frames_host", C.c_int32(n), C.c_void_p(g0.data_ptr()), C.c_void_p(g1.data_ptr()), cams,
                    C.byref(make_field(field)), C.c_uint32(int(frame0) & 0xFFFFFFFF),

@@ -41,6 +41,8 @@ class Field:
     amps: np.ndarray           # [n]
     constant: float = 0.0
     mask: tuple | None = None  # (f1, f2, g) of the sinusoidal occlusion mask
+    rgb: np.ndarray | None = None       # [n, 3] lobe colours (a coloured field; amps unused)
+    constant_rgb: tuple | None = None   # the constant's colour (with rgb)
 
 
 @dataclasses.dataclass
@@ -462,6 +464,16 @@ class QuadScene:
     def gbuffer_on(self, t, device):
         """(g0, g1, g0_prev) of frame t as contiguous float32 tensors on device."""
         return tuple(a.contiguous() for a in self._gbuffer(_TORCH(device), t))
+
+
+def coloured(fld, seed):
+    """The same field with each lobe and the constant given a colour drawn
+    from the seed (channels in [0.2, 1.5] times the monochrome amplitude)."""
+    rng = np.random.default_rng(seed + 101)
+    n = len(fld.kappas)
+    rgb = np.asarray(fld.amps, np.float64)[:, None] * rng.uniform(0.2, 1.5, (n, 3))
+    c = tuple(float(fld.constant) * rng.uniform(0.2, 1.5, 3))
+    return dataclasses.replace(fld, rgb=rgb, constant_rgb=c)
 
 
 def eight_lobe_field(seed):

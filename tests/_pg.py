@@ -22,9 +22,12 @@ def ocam(cam):
 
 def ofld(fld):
     f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    rgb = getattr(fld, "rgb", None)
     return O.make_field(f32(fld.dirs), f32(fld.kappas), f32(fld.amps),
                         float(np.float32(fld.constant)),
-                        None if fld.mask is None else [float(np.float32(m)) for m in fld.mask])
+                        None if fld.mask is None else [float(np.float32(m)) for m in fld.mask],
+                        None if rgb is None else f32(rgb),
+                        None if rgb is None else f32(fld.constant_rgb))
 
 
 def dev(a):
