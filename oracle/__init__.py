@@ -100,6 +100,7 @@ def _load():
                 "or_adam": [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double,
                             C.c_double, C.c_double, C.c_double],
                 "or_reuse_picks": [_P, C.c_double, C.c_uint32, C.c_uint32, _P, _P, _P],
+                "or_frame_pixels": [_P, _P, _P, C.c_uint32, _P, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P],
                 "or_brdf_cos_f0": [C.c_double, C.c_double, C.c_double, _P, _P],
                 "or_dielectric_fresnel": [C.c_double],
             }
@@ -360,6 +361,24 @@ def reuse_picks(cfg, k, pix, frame_idx):
     n = _load().or_reuse_picks(C.byref(cfg), float(k), int(pix) & 0xFFFFFFFF, int(frame_idx) & 0xFFFFFFFF,
                                _ptr(dx), _ptr(dy), _ptr(sm))
     return dx[:n].copy(), dy[:n].copy(), sm[:n].copy()
+
+
+def frame_pixels(cfg, cam, field, frame_idx, g0, g1, g0_prev, gam_prev_row, xs, ys):
+    """Chosen pixels of one frame, each computed alone, from a previous Gamma
+    that is gam_prev_row for every pixel. Returns (gamma [n, 8], img [n] or
+    [n, 3] for a coloured field, margin [n])."""
+    hw = cfg.width * cfg.height
+    g0, g1, g0p = _f32(g0, (hw, 4)), _f32(g1, (hw, 4)), _f32(g0_prev, (hw, 4))
+    row = _f64(gam_prev_row, (8,))
+    xs = np.ascontiguousarray(xs, np.int32)
+    ys = np.ascontiguousarray(ys, np.int32)
+    n = len(xs)
+    planes = 3 if field.rgb else 1
+    out, img, margin = np.empty((n, 8)), np.empty(n * planes), np.empty(n)
+    _load().or_frame_pixels(C.byref(cfg), C.byref(cam), C.byref(field), int(frame_idx) & 0xFFFFFFFF,
+                            _ptr(g0), _ptr(g1), _ptr(g0p), _ptr(row), int(n), _ptr(xs), _ptr(ys),
+                            _ptr(out), _ptr(img), _ptr(margin))
+    return out, (img if planes == 1 else img.reshape(n, 3)), margin
 
 
 def frame(cfg, cam, field, frame_idx, g0, g1, g0_prev, gam_prev):

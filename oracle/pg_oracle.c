@@ -617,8 +617,8 @@ static void frame_change(const double np_[3], const double nc[3], double *gm)
 
 /* One pixel of the reprojection step. Returns accept; writes q (-1 if off
  * screen) and the reprojected / re-initialised Gamma. */
-static int reproject_pixel(const or_config *cfg, int x, int y, const float *g0, const float *g1,
-                           const float *g0p, const double *gam_prev, double *out, int32_t *q)
+static int reproject_pixel_s(const or_config *cfg, int x, int y, const float *g0, const float *g1,
+                             const float *g0p, const double *gam_prev, int64_t gstride, double *out, int32_t *q)
 {
     int W = cfg->width, H = cfg->height;
     int64_t i = (int64_t)y * W + x;
@@ -640,7 +640,7 @@ static int reproject_pixel(const or_config *cfg, int x, int y, const float *g0, 
         volatile float ndot = (n0 + n1) + n2;
         acc = (fabsf(dd) <= dlim) && (ndot >= (float)cfg->normal_tol);
         if (acc) {
-            memcpy(out, gam_prev + 8 * j, 8 * sizeof(double));
+            memcpy(out, gam_prev + gstride * j, 8 * sizeof(double));
             int same = memcmp(&g0p[4 * j], &g0[4 * i], 3 * sizeof(float)) == 0;
             if (!same) {
                 double np_[3] = {g0p[4 * j], g0p[4 * j + 1], g0p[4 * j + 2]};
@@ -651,6 +651,12 @@ static int reproject_pixel(const or_config *cfg, int x, int y, const float *g0, 
     }
     if (!acc) init_gamma(cfg, cfg->pi_reinit, out);
     return acc;
+}
+
+static int reproject_pixel(const or_config *cfg, int x, int y, const float *g0, const float *g1,
+                           const float *g0p, const double *gam_prev, double *out, int32_t *q)
+{
+    return reproject_pixel_s(cfg, x, y, g0, g1, g0p, gam_prev, 8, out, q);
 }
 
 void or_reproject(const or_config *cfg, const float *g0, const float *g1, const float *g0p,
@@ -795,18 +801,21 @@ static int draw_direction(const pixel_ctx *p, const uint32_t key[2], uint32_t pi
     return strat;
 }
 
-static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_field *fld,
-                         uint32_t frame, int x, int y, const float *g0, const float *g1,
-                         const double *gm, int reinit, or_samples *S, double *img)
+/* Sampling of pixel (x, y); its outputs go to slot `slot` of planes of
+ * `stride` entries (the whole frame: slot = pixel index, stride = W H). */
+static void sample_pixel_s(const or_config *cfg, const or_camera *cam, const or_field *fld,
+                           uint32_t frame, int x, int y, const float *g0, const float *g1,
+                           const double *gm, int reinit, or_samples *S, double *img, int64_t slot,
+                           int64_t stride)
 {
-    int W = cfg->width, H = cfg->height, spp = cfg->spp;
-    int64_t i = (int64_t)y * W + x, HW = (int64_t)W * H;
+    int W = cfg->width, spp = cfg->spp;
+    int64_t i = (int64_t)y * W + x;
     pixel_ctx p;
     pixel_setup(cfg, cam, x, y, g0, g1, gm, reinit, &p);
     uint32_t key[2] = {cfg->seed_lo, cfg->seed_hi};
     double sum = 0.0, sum_rgb[3] = {0.0, 0.0, 0.0};
     for (int s = 0; s < spp; ++s) {
-        int64_t o = (int64_t)s * HW + i;
+        int64_t o = (int64_t)s * stride + slot;
         double wl[3], u[2], margin;
         int valid, have_u;
         int strat = draw_direction(&p, key, (uint32_t)i, frame, (uint32_t)s, 0u, wl, u, &have_u, &valid,
@@ -856,10 +865,18 @@ static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_fi
         }
     }
     if (fld->rgb) {
-        for (int k = 0; k < 3; ++k) img[k * HW + i] = sum_rgb[k] / spp;
+        for (int k = 0; k < 3; ++k) img[k * stride + slot] = sum_rgb[k] / spp;
     } else {
-        img[i] = sum / spp;
+        img[slot] = sum / spp;
     }
+}
+
+static void sample_pixel(const or_config *cfg, const or_camera *cam, const or_field *fld,
+                         uint32_t frame, int x, int y, const float *g0, const float *g1,
+                         const double *gm, int reinit, or_samples *S, double *img)
+{
+    sample_pixel_s(cfg, cam, fld, frame, x, y, g0, g1, gm, reinit, S, img, (int64_t)y * cfg->width + x,
+                   (int64_t)cfg->width * cfg->height);
 }
 
 void or_sample(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,
@@ -897,19 +914,32 @@ void or_sample(const or_config *cfg, const or_camera *cam, const or_field *fld, 
 /* ------------------------------------------------------------------------ */
 static void em_step(const or_config *cfg, double *gm, double a, double b, double s1x, double s1y,
                     double s2xx, double s2yy, double s2xy);
+static void update_pixel_s(const or_config *cfg, const or_camera *cam, int x, int y,
+                           const float *g0, const float *g1, double *gm, int reinit,
+                           const double *wx, const double *wy, const double *wz,
+                           const double *rad, const uint8_t *strat, int64_t slot, int64_t stride);
 
 static void update_pixel(const or_config *cfg, const or_camera *cam, int x, int y,
                          const float *g0, const float *g1, double *gm, int reinit,
                          const double *wx, const double *wy, const double *wz,
                          const double *rad, const uint8_t *strat)
 {
-    int W = cfg->width, H = cfg->height, spp = cfg->spp;
-    int64_t i = (int64_t)y * W + x, HW = (int64_t)W * H;
+    int64_t i = (int64_t)y * cfg->width + x;
+    update_pixel_s(cfg, cam, x, y, g0, g1, gm, reinit, wx, wy, wz, rad, strat, i,
+                   (int64_t)cfg->width * cfg->height);
+}
+
+static void update_pixel_s(const or_config *cfg, const or_camera *cam, int x, int y,
+                           const float *g0, const float *g1, double *gm, int reinit,
+                           const double *wx, const double *wy, const double *wz,
+                           const double *rad, const uint8_t *strat, int64_t slot, int64_t stride)
+{
+    int spp = cfg->spp;
     pixel_ctx p;
     pixel_setup(cfg, cam, x, y, g0, g1, gm, reinit, &p);
     double a = 0, b = 0, s1x = 0, s1y = 0, s2xx = 0, s2yy = 0, s2xy = 0;
     for (int s = 0; s < spp; ++s) {
-        int64_t o = (int64_t)s * HW + i;
+        int64_t o = (int64_t)s * stride + slot;
         if (strat[o] != S_BRDF) continue; /* guide draws, fallbacks and wasted draws do not train */
         double ww[3] = {wx[o], wy[o], wz[o]}, wl[3];
         to_local(p.n, ww, wl);
@@ -1091,6 +1121,45 @@ static void update_pixel_reuse(const or_config *cfg, const or_camera *cam, uint3
     }
     free(dx);
     em_step(cfg, gm, acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6]);
+}
+
+/* Chosen pixels (xs[k], ys[k]) of one frame, each computed alone (no
+ * neighbour reuse): reprojection against a previous Gamma that is the same
+ * row gam_prev_row for every pixel (a screen's first frame), sampling and
+ * training. Writes each pixel's new Gamma (gam_out[8k..]), its estimate
+ * (img[k * planes + c], planes = 3 for a coloured field, else 1) and the
+ * smallest decision margin of its draws. For parity checks of full-size
+ * frames on a sample of their pixels. */
+void or_frame_pixels(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,
+                     const float *g0, const float *g1, const float *g0p, const double *gam_prev_row,
+                     int64_t n, const int32_t *xs, const int32_t *ys, double *gam_out, double *img,
+                     double *margin)
+{
+    int spp = cfg->spp, planes = fld->rgb ? 3 : 1;
+#pragma omp parallel
+    {
+        double *buf = malloc(sizeof(double) * 12 * (size_t)spp);
+        uint8_t *strat = malloc((size_t)spp);
+        or_samples S = {.wx = buf, .wy = buf + spp, .wz = buf + 2 * spp, .radiance = buf + 3 * spp,
+                        .pdf = buf + 4 * spp, .mis = buf + 5 * spp, .estimate = buf + 6 * spp,
+                        .strategy = strat, .pg = buf + 7 * spp, .pb = buf + 8 * spp, .ux = buf + 9 * spp,
+                        .uy = buf + 10 * spp, .margin = buf + 11 * spp};
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t k = 0; k < n; ++k) {
+            int x = xs[k], y = ys[k];
+            int32_t q;
+            double *gm = gam_out + 8 * k, im[3];
+            int acc = reproject_pixel_s(cfg, x, y, g0, g1, g0p, gam_prev_row, 0, gm, &q);
+            sample_pixel_s(cfg, cam, fld, frame, x, y, g0, g1, gm, !acc, &S, im, 0, 1);
+            update_pixel_s(cfg, cam, x, y, g0, g1, gm, !acc, S.wx, S.wy, S.wz, S.radiance, S.strategy, 0, 1);
+            double m = 1.0;
+            for (int t = 0; t < spp; ++t) m = S.margin[t] < m ? S.margin[t] : m;
+            margin[k] = m;
+            for (int c = 0; c < planes; ++c) img[k * planes + c] = im[c];
+        }
+        free(buf);
+        free(strat);
+    }
 }
 
 /* One whole frame: reprojection, sampling and training, pixel by pixel.

@@ -53,8 +53,10 @@ def test_config_default_and_validation_without_gpu(lib):
     assert abs(cfg.pi_reinit - 0.05) < 1e-7
     h = C.c_void_p()
     # invalid configurations are rejected on the host before any device work
-    for field, bad in (("width", 0), ("spp", 0), ("gamma_dtype", 7), ("pi_min", 0.99),
-                       ("rho_max", 1.0), ("sigma2_min", 0.0)):
+    for field, bad in (("width", 0), ("height", 32769), ("spp", 0), ("spp", 1025), ("gamma_dtype", 7),
+                       ("pi_min", 0.99), ("rho_max", 1.0), ("sigma2_min", 0.0), ("reuse_radius", 9),
+                       ("reuse_radius", -1), ("stochastic_round", 2), ("ggx_f0", 1.5), ("ggx_f0", -0.1),
+                       ("transparent", 2)):
         c2 = _lib.pg_config()
         C.memmove(C.byref(c2), C.byref(cfg), C.sizeof(cfg))
         setattr(c2, field, bad)
@@ -64,6 +66,7 @@ def test_config_default_and_validation_without_gpu(lib):
     # NULL contexts are rejected, not dereferenced
     assert lib.pg_frame(None, None, None, None, 0, None) == _lib.PG_ERR_ARG
     assert lib.pg_reproject(None, None, None, None) == _lib.PG_ERR_ARG
+    assert lib.pg_frames_host(None, 1, None, None, None, None, 0, None, None) == _lib.PG_ERR_ARG
     assert lib.pg_check(None) == _lib.PG_ERR_ARG
     assert lib.pg_gamma_bytes(None) == 0
     lib.pg_destroy(None)
