@@ -37,11 +37,16 @@ REUSE_R = 2
 # cache) and writes Gamma(t) (16 B)
 BYTES_PER_PIXEL["reuse"] = (64 + 4 + 20) + (64 + 20 + 16)
 REF_SPP = 256
+# one projected Adam step on FP16 Gamma: Gamma read + write (32 B), the
+# gradient (24 B), m and v each read and written (4 x 24 B in binary32,
+# 4 x 12 B in BF16)
+ADAM_BYTES_PER_PIXEL = {"f32": 32 + 24 + 96, "bf16": 32 + 24 + 48}
 
 
-def kernel_traffic():
-    """DRAM bytes per k_frame<F16> launch from the committed ncu summary, or None
-    when the kernel sources changed since those counters were taken."""
+def kernel_counters():
+    """(DRAM bytes, warp instructions) per k_frame<F16> launch from the
+    committed ncu summary, each None when absent or when the kernel sources
+    changed since those counters were taken."""
     import hashlib
     prof = os.path.join(ROOT, "profiles", "k_frame_1080p_pan.md")
     src = os.path.join(ROOT, "paper_2112_09728_gb300", "csrc")
@@ -50,16 +55,34 @@ def kernel_traffic():
         for f in ("pg_device.cuh", "pg_kernels.cu", "pg_launch.h"):
             with open(os.path.join(src, f), "rb") as fh:
                 h.update(fh.read())
-        sha, traffic = None, None
+        sha, traffic, inst = None, None, None
         with open(prof) as fh:
             for line in fh:
                 if line.startswith("kernel sources sha256"):
                     sha = line.split(":")[1].strip()
                 elif line.startswith("traffic_bytes_per_launch:"):
                     traffic = float(line.split(":")[1])
-        return traffic if sha == h.hexdigest() else None
+                elif line.startswith("warp_instructions_per_launch:"):
+                    inst = float(line.split(":")[1])
+        return (traffic, inst) if sha == h.hexdigest() else (None, None)
     except Exception:
+        return None, None
+
+
+def issue_roofline(inst, ms, sm_mhz):
+    """Instruction issue of the fused kernel: warp instructions per launch
+    (ncu) over the live-measured launch time, against one warp instruction
+    per cycle on each of the 4 schedulers of every SM at the SM clock
+    sampled during the timed frames."""
+    import torch
+    if inst is None or not ms:
         return None
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = sm_mhz or 2070.0
+    peak = sms * 4 * mhz * 1e6
+    ach = inst / (ms * 1e-3)
+    return {"achieved": ach, "peak": peak, "unit": "warp instructions/s", "frac": ach / peak,
+            "warp_instructions_per_launch": inst, "sms": sms, "sm_mhz": mhz}
 
 
 def measured_hbm():
@@ -318,13 +341,16 @@ def run_e2e(par, sc, fld, g0h, g1h, gamma_dtype, warmup, steps, seed_offset):
 def run_4k(par, fld, sc, warmup, steps, flush):
     """3840x2160, 4 spp, FP16 Gamma: per frame the fused EM pass, then one
     gradient step (second-moment adjoint with 4 draws per pixel and a projected
-    Adam step); each part timed with CUDA events, L2 flushed before each frame.
-    G-buffers are generated on the device before timing."""
+    Adam step with BF16 moments); each part timed with CUDA events, L2 flushed
+    before each frame. G-buffers are generated on the device before timing.
+    The Adam step with binary32 moments is timed beside it on the last
+    gradient."""
     import torch
     from paper_2112_09728_gb300.guide import GuidePass
     hw = par.width * par.height
     frames = [sc.gbuffer_on(t, "cuda") for t in range(warmup + steps)]
-    gp = GuidePass(par.width, par.height, spp=par.spp, gamma_dtype="f16", seed=par.seed, init_pi=par.init_pi)
+    gp = GuidePass(par.width, par.height, spp=par.spp, gamma_dtype="f16", seed=par.seed, init_pi=par.init_pi,
+                   adam_dtype="bf16")
     img = torch.empty(hw, device="cuda")
     loss = torch.empty(hw, device="cuda")
     grad = torch.empty((6, hw), device="cuda")
@@ -335,19 +361,34 @@ def run_4k(par, fld, sc, warmup, steps, flush):
         timed = t >= warmup
         if timed:
             flush.zero_()
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ev[0].record()
         gp.pg_frame(g0, g1, cam, g0p, fld, t, img)
         if timed:
             ev[1].record()
         gp.pg_grad(g0, g1, cam, fld, t, par.spp, loss=loss, grad=grad)
-        gp.pg_adam_step(grad, lr=1e-2, step=t + 1)
         if timed:
             ev[2].record()
+        gp.pg_adam_step(grad, lr=1e-2, step=t + 1)
+        if timed:
+            ev[3].record()
             t_frame.append(ev)
     torch.cuda.synchronize()
     gp.pg_check()
     gp.close()
+    # the same Adam step with binary32 moments (48 more bytes per pixel)
+    g32 = GuidePass(par.width, par.height, spp=par.spp, gamma_dtype="f16", seed=par.seed, init_pi=par.init_pi)
+    t32 = []
+    for t in range(warmup + steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        g32.pg_adam_step(grad, lr=1e-2, step=t + 1)
+        ev[1].record()
+        if t >= warmup:
+            t32.append(ev)
+    torch.cuda.synchronize()
+    g32.close()
     # rejection rate of the timed frames, from the staged reprojection's accept mask
     acc = torch.empty(hw, dtype=torch.uint8, device="cuda")
     rej = []
@@ -357,13 +398,19 @@ def run_4k(par, fld, sc, warmup, steps, flush):
         chk.pg_reproject(g0, g1, sc.camera(t), g0p, acc)
         rej.append(1.0 - float(acc.float().mean()))
         chk.close()
-    fm = [e[0].elapsed_time(e[1]) for e in t_frame]
-    gm = [e[1].elapsed_time(e[2]) for e in t_frame]
-    f, g = sum(fm) / len(fm), sum(gm) / len(gm)
+    mean = lambda xs: sum(xs) / len(xs)
+    f = mean([e[0].elapsed_time(e[1]) for e in t_frame])
+    gr = mean([e[1].elapsed_time(e[2]) for e in t_frame])
+    ad = mean([e[2].elapsed_time(e[3]) for e in t_frame])
+    ad32 = mean([e[0].elapsed_time(e[1]) for e in t32])
+    g = gr + ad
     peak, _ = measured_hbm()
     return {"workload": "3840x2160, 4 spp, FP16 Gamma: camera orbiting 0.5 deg/frame over a normal-mapped ground "
                         "with 16 occluding quads, GGX U(0.02,1), 8 vMF lobes x mask",
-            "frames_timed": steps, "frame_ms": f, "grad_adam_ms": g,
+            "frames_timed": steps, "frame_ms": f, "grad_adam_ms": g, "grad_ms": gr,
+            "adam_ms": ad, "adam_moments": "bf16 (stochastically rounded)", "adam_f32_moments_ms": ad32,
+            "adam_hbm_frac": ADAM_BYTES_PER_PIXEL["bf16"] * hw / (ad * 1e-3) / 1e9 / peak,
+            "adam_f32_moments_hbm_frac": ADAM_BYTES_PER_PIXEL["f32"] * hw / (ad32 * 1e-3) / 1e9 / peak,
             "frame_mpix_s": hw / f / 1e3, "step_mpix_s": hw / (f + g) / 1e3,
             "frame_hbm_frac": BYTES_PER_PIXEL["f16"] * hw / (f * 1e-3) / 1e9 / peak,
             "rejection_rate": sum(rej) / len(rej), "kernels_per_frame": 3}
@@ -484,7 +531,8 @@ def orbit_step(width, height, frames=4):
     __graft_entry__.build()
     wl = scenes.workload_4k(width, height)
     par, fld, sc = wl["params"], wl["field"], wl["scene"]
-    gp = GuidePass(width, height, spp=par.spp, gamma_dtype="f16", seed=par.seed, init_pi=par.init_pi)
+    gp = GuidePass(width, height, spp=par.spp, gamma_dtype="f16", seed=par.seed, init_pi=par.init_pi,
+                   adam_dtype="bf16")
     hw = width * height
     img, loss = torch.empty(hw, device="cuda"), torch.empty(hw, device="cuda")
     grad = torch.empty((6, hw), device="cuda")
@@ -629,6 +677,7 @@ def run_gpu(args, ws, rank, local):
         return
     peak, peak_kind = measured_hbm()
     main = res["f16"]
+    traffic, inst = kernel_counters()
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
         px, sec, steps = oracle_strip_frames(16, args.cpu_budget)
@@ -656,8 +705,9 @@ def run_gpu(args, ws, rank, local):
         "roofline": {"bound": "hbm", "achieved": main["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": main["gbs"] / peak, "peak_kind": peak_kind,
                      "kernel": "k_frame<f16> (fused guide pass)",
-                     "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL["f16"], "traffic": kernel_traffic(),
-                     "traffic_unit": "bytes per launch (ncu dram read+write, profiles/k_frame_1080p_pan.md)"},
+                     "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL["f16"], "traffic": traffic,
+                     "traffic_unit": "bytes per launch (ncu dram read+write, profiles/k_frame_1080p_pan.md)",
+                     "issue": issue_roofline(inst, main["ms_per_step"], (clocks or {}).get("sm_mhz"))},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_v, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "pg_frames_host (C ABI, host buffers): page-locked G-buffer uploads and image "

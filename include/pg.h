@@ -91,7 +91,13 @@ typedef enum { PG_F32 = 0, PG_F16 = 1, PG_BF16 = 2 } pg_dtype;
  * [0, 1]: f_r carries F = F0 + (1 - F0)(1 - o.h)^5; 1 gives F = 1.
  * transparent [0] 1 enables the transparent material (roughness codes
  * <= -1.5, see pg_gbuffer); with 0 every negative roughness code is
- * Lambertian and the fused kernel carries none of the transparent code. */
+ * Lambertian and the fused kernel carries none of the transparent code.
+ * adam_dtype [PG_F32] storage of the Adam moments m and v of pg_adam_step:
+ * PG_F32, or PG_BF16 (12 bytes per pixel per moment instead of 24). BF16
+ * moments are rounded stochastically when stored (round to nearest would
+ * freeze v, whose update with beta2 = 0.999 is a thousandth of its value,
+ * well below BF16's half ulp of 2^-9); the arithmetic is binary32 either
+ * way. PG_F16 is refused (g^2 leaves its range). */
 typedef struct {
     int32_t width, height;   /* screen size in pixels, each in [1, 32768] */
     int32_t spp;             /* samples per pixel per frame, in [1, 1024] */
@@ -105,6 +111,7 @@ typedef struct {
     int32_t stochastic_round;
     float ggx_f0;
     int32_t transparent;
+    int32_t adam_dtype;      /* pg_dtype: PG_F32 or PG_BF16 */
 } pg_config;
 
 /* Camera of one frame: the primary ray of pixel (x, y). Orthographic (kind 0):
@@ -283,9 +290,24 @@ pg_status pg_grad(pg_ctx *ctx, const pg_gbuffer *cur, const pg_field *field, uin
  * ([6][H*W]), projected back onto the guide's domain (mean in [0,1]^2,
  * variances >= sigma2_min, |rho| <= rho_max, pi in [pi_min, pi_max]) and
  * written into Gamma as moments; k and W are kept. The context owns the
- * moments (allocated on first use); step = 1 restarts them from zero. */
+ * moments (allocated on first use: binary32 [6][H*W] planes, or with BF16 one
+ * 24-byte record {m_0..m_5, v_0..v_5} per pixel); step = 1 restarts them
+ * from zero. The new m and v are formed in binary32 and the step uses them
+ * before they are stored; with BF16 moments, moment n (m_0..m_5, then
+ * v_0..v_5) of pixel i is stored stochastically with the 16 bits of Philox
+ * word n/2 (of the 8 words of the calls at counters (i, step, 0, 6) and
+ * (i, step, 1, 6)) at bit 16 (n mod 2) and up, as Gamma is under
+ * stochastic_round. */
 pg_status pg_adam_step(pg_ctx *ctx, const float *d_grad, float lr, float beta1, float beta2, float eps,
                        int32_t step);
+
+/* The Adam moments m and v as binary32 [6][H*W] device planes: checkpoint
+ * (get) and resume (set; BF16 moments are rounded to nearest, so values got
+ * from a BF16 context are restored exactly). Resume by setting Gamma and the
+ * moments, then calling pg_adam_step with the next step number. get fails
+ * with PG_ERR_STATE before the first pg_adam_step or pg_set_adam_state. */
+pg_status pg_get_adam_state(pg_ctx *ctx, float *d_m, float *d_v);
+pg_status pg_set_adam_state(pg_ctx *ctx, const float *d_m, const float *d_v);
 
 /* theta of every pixel ([6][H*W] planes) from Gamma, and back (projected as
  * in pg_adam_step; k and W are kept). */

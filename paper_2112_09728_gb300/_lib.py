@@ -25,7 +25,7 @@ class pg_config(C.Structure):
                 ("sigma2_min", C.c_float), ("rho_max", C.c_float), ("init_mu", C.c_float * 2),
                 ("init_sigma", C.c_float * 3), ("init_pi", C.c_float), ("reuse_radius", C.c_int32),
                 ("stochastic_round", C.c_int32), ("ggx_f0", C.c_float),
-                ("transparent", C.c_int32)]
+                ("transparent", C.c_int32), ("adam_dtype", C.c_int32)]
 
 
 class pg_camera(C.Structure):
@@ -74,6 +74,8 @@ _SIGNATURES = {
     "pg_philox": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int32, _P]),
     "pg_grad": (C.c_int, [_P, C.POINTER(pg_gbuffer), C.POINTER(pg_field), C.c_uint32, C.c_int32, _P, _P, _P]),
     "pg_adam_step": (C.c_int, [_P, _P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32]),
+    "pg_get_adam_state": (C.c_int, [_P, _P, _P]),
+    "pg_set_adam_state": (C.c_int, [_P, _P, _P]),
     "pg_theta_from_gamma": (C.c_int, [_P, _P]),
     "pg_theta_to_gamma": (C.c_int, [_P, _P]),
     "pg_frame_noalloc": (C.c_int, [C.POINTER(pg_config), C.POINTER(pg_gbuffer), _P, C.POINTER(pg_field), C.c_uint32,

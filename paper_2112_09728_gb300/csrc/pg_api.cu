@@ -22,8 +22,10 @@ struct pg_ctx {
     int phase = 0;            // 1 between pg_reproject and pg_update
     int* d_err = nullptr;     // device flag: non-finite Gamma stored
     uint32_t sample_frame = 0;  // frame of the last pg_sample (rounding bits of pg_update)
-    float* adam_m = nullptr;  // Adam moments of theta, [6][H*W] each (allocated on first use)
-    float* adam_v = nullptr;
+    // Adam moments of theta (allocated on first use): binary32 [6][H*W] planes
+    // in adam_m and adam_v, or BF16 records of 24 bytes per pixel in adam_m alone
+    void* adam_m = nullptr;
+    void* adam_v = nullptr;
     float4* vpl = nullptr;    // neighbour reuse: one VPL per sample {world direction, radiance}
     float* vpl_pb = nullptr;  //   and the density of its BRDF draw (0: does not train)
     float* zbuf = nullptr;    //   and each pixel's rectangle mass Z, from the path-tracing pass
@@ -454,6 +456,22 @@ pg_status pg_grad(pg_ctx* c, const pg_gbuffer* cur, const pg_field* field, uint3
     return PG_OK;
 }
 
+static bool adam_bf16(const pg_ctx* c) { return c->cfg.adam_dtype == PG_BF16; }
+
+static pg_status ensure_adam(pg_ctx* c, const char* where) {
+    if (c->adam_m) return PG_OK;
+    const size_t bytes = 6 * hw_of(c) * sizeof(float);   // one plane set, or both BF16 moments
+    bool ok = cudaMalloc(&c->adam_m, bytes) == cudaSuccess;
+    if (ok && !adam_bf16(c)) ok = cudaMalloc(&c->adam_v, bytes) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (c->adam_m) cudaFree(c->adam_m);
+        c->adam_m = c->adam_v = nullptr;
+        return fail(c, PG_ERR_OOM, where);
+    }
+    return PG_OK;
+}
+
 pg_status pg_adam_step(pg_ctx* c, const float* d_grad, float lr, float beta1, float beta2, float eps, int32_t step) {
     if (!c) return PG_ERR_ARG;
     if (c->phase != 0) return fail(c, PG_ERR_STATE, "pg_adam_step: a staged frame is in progress");
@@ -461,26 +479,58 @@ pg_status pg_adam_step(pg_ctx* c, const float* d_grad, float lr, float beta1, fl
     if (step < 1 || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) ||
         !std::isfinite(lr))
         return fail(c, PG_ERR_ARG, "pg_adam_step: need step >= 1, 0 <= beta < 1, eps > 0, finite lr");
+    pg_status s = ensure_adam(c, "pg_adam_step: cannot allocate the Adam moments");
+    if (s != PG_OK) return s;
     const size_t bytes = 6 * hw_of(c) * sizeof(float);
-    if (!c->adam_m) {
-        if (cudaMalloc(&c->adam_m, bytes) != cudaSuccess || cudaMalloc(&c->adam_v, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            if (c->adam_m) cudaFree(c->adam_m);
-            c->adam_m = c->adam_v = nullptr;
-            return fail(c, PG_ERR_OOM, "pg_adam_step: cannot allocate the Adam moments");
-        }
-    }
     cudaError_t e = cudaSuccess;
     if (step == 1) {   // a new run of steps starts from zero moments
         e = cudaMemsetAsync(c->adam_m, 0, bytes, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->adam_v, 0, bytes, c->stream);
+        if (e == cudaSuccess && c->adam_v) e = cudaMemsetAsync(c->adam_v, 0, bytes, c->stream);
     }
     const float c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, step)));
     const float c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, step)));
-    if (e == cudaSuccess)
-        e = pgk::launch_adam(c->cfg.gamma_dtype, c->base, c->gam[c->cur], d_grad, c->adam_m, c->adam_v, lr, beta1,
-                             beta2, eps, c1, c2, c->stream);
+    if (e == cudaSuccess) {
+        if (adam_bf16(c))
+            e = pgk::launch_adam_bf16(c->cfg.gamma_dtype, c->base, c->gam[c->cur], d_grad, c->adam_m, lr, beta1,
+                                      beta2, eps, c1, c2, (uint32_t)step, c->stream);
+        else
+            e = pgk::launch_adam(c->cfg.gamma_dtype, c->base, c->gam[c->cur], d_grad, (float*)c->adam_m,
+                                 (float*)c->adam_v, lr, beta1, beta2, eps, c1, c2, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "pg_adam_step");
+    return PG_OK;
+}
+
+pg_status pg_get_adam_state(pg_ctx* c, float* d_m, float* d_v) {
+    if (!c) return PG_ERR_ARG;
+    if (!d_m || !d_v || d_m == d_v) return fail(c, PG_ERR_ARG, "pg_get_adam_state: need two distinct buffers");
+    if (!c->adam_m) return fail(c, PG_ERR_STATE, "pg_get_adam_state: no Adam step has run");
+    const size_t bytes = 6 * hw_of(c) * sizeof(float);
+    cudaError_t e;
+    if (adam_bf16(c)) {
+        e = pgk::launch_adam_rec_get(c->base, c->adam_m, d_m, d_v, c->stream);
+    } else {
+        e = cudaMemcpyAsync(d_m, c->adam_m, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_v, c->adam_v, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "pg_get_adam_state");
+    return PG_OK;
+}
+
+pg_status pg_set_adam_state(pg_ctx* c, const float* d_m, const float* d_v) {
+    if (!c) return PG_ERR_ARG;
+    if (!d_m || !d_v) return fail(c, PG_ERR_ARG, "pg_set_adam_state: NULL argument");
+    pg_status s = ensure_adam(c, "pg_set_adam_state: cannot allocate the Adam moments");
+    if (s != PG_OK) return s;
+    const size_t bytes = 6 * hw_of(c) * sizeof(float);
+    cudaError_t e;
+    if (adam_bf16(c)) {
+        e = pgk::launch_adam_rec_set(c->base, d_m, d_v, c->adam_m, c->stream);
+    } else {
+        e = cudaMemcpyAsync(c->adam_m, d_m, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->adam_v, d_v, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "pg_set_adam_state");
     return PG_OK;
 }
 

@@ -500,6 +500,26 @@ __device__ __forceinline__ void set_theta(const Params& P, Gam& g, const float t
 
 // One Adam step (Kingma & Ba 2015) on theta with projection; c1, c2 are the
 // bias corrections 1/(1 - b1^t), 1/(1 - b2^t) of step t.
+// One projected Adam step on theta of a pixel from its gradient and the old
+// moments (binary32 arithmetic); returns the new moments in mk, vk.
+template <int DT>
+__device__ __forceinline__ void adam_pixel(const Params& P, void* gam, size_t hw, size_t i, const float gk[6],
+                                           const float mo[6], const float vo[6], float mk[6], float vk[6], float lr,
+                                           float b1, float b2, float eps, float c1, float c2) {
+    Gam g = Store<DT>::load(gam, hw, i);
+    float th[6];
+    theta_of(P, g, th);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        mk[k] = fmaf(b1, mo[k], (1.0f - b1) * gk[k]);
+        vk[k] = fmaf(b2, vo[k], (1.0f - b2) * gk[k] * gk[k]);
+        th[k] -= lr * fdiv(mk[k] * c1, sqrtf(vk[k] * c2) + eps);
+    }
+    set_theta(P, g, th);
+    Store<DT>::store(gam, hw, i, g);
+}
+
+// Binary32 moments: [6][H*W] planes each, one pixel per thread.
 template <int DT>
 __global__ void __launch_bounds__(kBlock) k_adam(const Params P, void* __restrict__ gam,
                                                  const float* __restrict__ grad, float* __restrict__ m,
@@ -523,6 +543,75 @@ __global__ void __launch_bounds__(kBlock) k_adam(const Params P, void* __restric
     }
     set_theta(P, g, th);
     Store<DT>::store(gam, hw, i, g);
+}
+
+// BF16 moments: one 24-byte record per pixel {m_0..m_5, v_0..v_5} (three
+// 8-byte words), read and written whole; each moment is stored stochastically
+// with 16 bits of the Philox calls at (pixel, step, 0, 6) and (pixel, step, 1, 6)
+// (moment n: word n/2, bits 16 (n mod 2) and up). A thread steps two pixels,
+// i and i + ceil(H*W / 2), for more loads in flight.
+template <int DT>
+__device__ __forceinline__ void adam_pixel_bf16(const Params& P, void* gam, const float* grad, uint2* rec,
+                                                size_t hw, size_t i, float lr, float b1, float b2, float eps,
+                                                float c1, float c2, uint32_t step) {
+    const uint2 r0 = rec[3 * i], r1 = rec[3 * i + 1], r2 = rec[3 * i + 2];
+    const uint32_t w[6] = {r0.x, r0.y, r1.x, r1.y, r2.x, r2.y};
+    float gk[6], mo[6], vo[6], mk[6], vk[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        gk[k] = grad[k * hw + i];
+        mo[k] = __uint_as_float((w[k >> 1] >> (16 * (k & 1))) << 16);
+        vo[k] = __uint_as_float((w[(k + 6) >> 1] >> (16 * (k & 1))) << 16);
+    }
+    adam_pixel<DT>(P, gam, hw, i, gk, mo, vo, mk, vk, lr, b1, b2, eps, c1, c2);
+    const uint4 ra = philox4x32_10(make_uint4((uint32_t)i, step, 0u, 6u), P.rk);
+    const uint4 rb = philox4x32_10(make_uint4((uint32_t)i, step, 1u, 6u), P.rk);
+    const uint32_t rw[6] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y};
+    uint32_t o[12];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        o[k] = sr_pack_bf16(mk[k], rw[k >> 1] >> (16 * (k & 1)));
+        o[k + 6] = sr_pack_bf16(vk[k], rw[(k + 6) >> 1] >> (16 * (k & 1)));
+    }
+    rec[3 * i] = make_uint2(o[0] | (o[1] << 16), o[2] | (o[3] << 16));
+    rec[3 * i + 1] = make_uint2(o[4] | (o[5] << 16), o[6] | (o[7] << 16));
+    rec[3 * i + 2] = make_uint2(o[8] | (o[9] << 16), o[10] | (o[11] << 16));
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kBlock) k_adam_bf16(const Params P, void* __restrict__ gam,
+                                                      const float* __restrict__ grad, uint2* __restrict__ rec,
+                                                      float lr, float b1, float b2, float eps, float c1, float c2,
+                                                      uint32_t step) {
+    const size_t hw = (size_t)P.W * P.H, half = (hw + 1) / 2;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= half) return;
+    adam_pixel_bf16<DT>(P, gam, grad, rec, hw, i, lr, b1, b2, eps, c1, c2, step);
+    if (i + half < hw) adam_pixel_bf16<DT>(P, gam, grad, rec, hw, i + half, lr, b1, b2, eps, c1, c2, step);
+}
+
+// BF16 moment records <-> binary32 [6][H*W] planes (checkpoint and resume;
+// the planes are rounded to nearest).
+__global__ void k_adam_rec_get(const uint16_t* __restrict__ rec, float* __restrict__ m, float* __restrict__ v,
+                               size_t hw) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hw) return;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        m[k * hw + i] = __uint_as_float((uint32_t)rec[12 * i + k] << 16);
+        v[k * hw + i] = __uint_as_float((uint32_t)rec[12 * i + 6 + k] << 16);
+    }
+}
+
+__global__ void k_adam_rec_set(const float* __restrict__ m, const float* __restrict__ v, uint16_t* __restrict__ rec,
+                               size_t hw) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= hw) return;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        rec[12 * i + k] = __bfloat16_as_ushort(__float2bfloat16_rn(m[k * hw + i]));
+        rec[12 * i + 6 + k] = __bfloat16_as_ushort(__float2bfloat16_rn(v[k * hw + i]));
+    }
 }
 
 template <int DT>
@@ -680,6 +769,26 @@ cudaError_t launch_grad(int dt, const Params& P, const void* gam, const float* t
 cudaError_t launch_adam(int dt, const Params& P, void* gam, const float* grad, float* m, float* v, float lr, float b1,
                         float b2, float eps, float c1, float c2, cudaStream_t st) {
     PG_DISPATCH(dt, (k_adam<D><<<grid_for(P), kBlock, 0, st>>>(P, gam, grad, m, v, lr, b1, b2, eps, c1, c2)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_bf16(int dt, const Params& P, void* gam, const float* grad, void* rec, float lr, float b1,
+                             float b2, float eps, float c1, float c2, uint32_t step, cudaStream_t st) {
+    const size_t half = ((size_t)P.W * P.H + 1) / 2;
+    const dim3 grid((unsigned)((half + kBlock - 1) / kBlock));
+    PG_DISPATCH(dt, (k_adam_bf16<D><<<grid, kBlock, 0, st>>>(P, gam, grad, reinterpret_cast<uint2*>(rec), lr, b1, b2,
+                                                              eps, c1, c2, step)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_rec_get(const Params& P, const void* rec, float* m, float* v, cudaStream_t st) {
+    k_adam_rec_get<<<grid_for(P), kBlock, 0, st>>>(reinterpret_cast<const uint16_t*>(rec), m, v,
+                                                     (size_t)P.W * P.H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_rec_set(const Params& P, const float* m, const float* v, void* rec, cudaStream_t st) {
+    k_adam_rec_set<<<grid_for(P), kBlock, 0, st>>>(m, v, reinterpret_cast<uint16_t*>(rec), (size_t)P.W * P.H);
     return cudaGetLastError();
 }
 

@@ -40,8 +40,15 @@ cudaError_t launch_from_f32(int dt, const Params& P, const float4* src, void* ds
 
 cudaError_t launch_grad(int dt, const Params& P, const void* gam, const float* theta, const float4* g0,
                         const float4* g1, uint32_t frame, int n, float* loss, float* grad, cudaStream_t st);
+// Adam: binary32 moments as [6][H*W] planes m and v; BF16 moments as one
+// 24-byte record per pixel {m_0..m_5, v_0..v_5} (rec), converted to and from
+// binary32 planes by the rec_get / rec_set launchers
 cudaError_t launch_adam(int dt, const Params& P, void* gam, const float* grad, float* m, float* v, float lr, float b1,
                         float b2, float eps, float c1, float c2, cudaStream_t st);
+cudaError_t launch_adam_bf16(int dt, const Params& P, void* gam, const float* grad, void* rec, float lr, float b1,
+                             float b2, float eps, float c1, float c2, uint32_t step, cudaStream_t st);
+cudaError_t launch_adam_rec_get(const Params& P, const void* rec, float* m, float* v, cudaStream_t st);
+cudaError_t launch_adam_rec_set(const Params& P, const float* m, const float* v, void* rec, cudaStream_t st);
 cudaError_t launch_theta_get(int dt, const Params& P, const void* gam, float* theta, cudaStream_t st);
 cudaError_t launch_theta_set(int dt, const Params& P, void* gam, const float* theta, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, int64_t n, uint32_t* out, bool curand,

@@ -81,6 +81,10 @@ pg_status check_config(const pg_config* c, std::string& why) {
     if (c->stochastic_round != 0 && c->stochastic_round != 1) { why = "stochastic_round must be 0 or 1"; return PG_ERR_ARG; }
     if (!(c->ggx_f0 >= 0.0f && c->ggx_f0 <= 1.0f)) { why = "ggx_f0 outside [0, 1]"; return PG_ERR_ARG; }
     if (c->transparent != 0 && c->transparent != 1) { why = "transparent must be 0 or 1"; return PG_ERR_ARG; }
+    if (c->adam_dtype != PG_F32 && c->adam_dtype != PG_BF16) {
+        why = "adam_dtype must be PG_F32 or PG_BF16";
+        return PG_ERR_ARG;
+    }
     return PG_OK;
 }
 

@@ -84,6 +84,8 @@ def make_config(width, height, spp=1, gamma_dtype="f32", seed=0, **overrides) ->
             getattr(cfg, k)[:] = [float(x) for x in v]
         elif k in ("k_max", "reuse_radius", "stochastic_round", "transparent"):
             setattr(cfg, k, int(v))
+        elif k == "adam_dtype":
+            cfg.adam_dtype = _DTYPES[v] if isinstance(v, str) else int(v)
         else:
             setattr(cfg, k, float(v))
     return cfg
@@ -233,6 +235,22 @@ class GuidePass:
         self._check_len(grad, 6 * self.hw, "grad")
         self._call("pg_adam_step", C.c_void_p(_ptr(grad, what="grad")), C.c_float(lr), C.c_float(beta1),
                    C.c_float(beta2), C.c_float(eps), C.c_int32(int(step)))
+
+    def pg_get_adam_state(self, m=None, v=None):
+        """The Adam moments (m, v) as float32 [6, H*W] planes."""
+        if m is None:
+            m = torch.empty((6, self.hw), dtype=torch.float32, device="cuda")
+        if v is None:
+            v = torch.empty((6, self.hw), dtype=torch.float32, device="cuda")
+        self._check_len(m, 6 * self.hw, "m")
+        self._check_len(v, 6 * self.hw, "v")
+        self._call("pg_get_adam_state", C.c_void_p(_ptr(m, what="m")), C.c_void_p(_ptr(v, what="v")))
+        return m, v
+
+    def pg_set_adam_state(self, m, v):
+        self._check_len(m, 6 * self.hw, "m")
+        self._check_len(v, 6 * self.hw, "v")
+        self._call("pg_set_adam_state", C.c_void_p(_ptr(m, what="m")), C.c_void_p(_ptr(v, what="v")))
 
     def pg_theta_from_gamma(self, theta=None):
         if theta is None:

@@ -39,14 +39,14 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
-def guide(par, gamma_dtype="f32"):
+def guide(par, gamma_dtype="f32", **kw):
     from paper_2112_09728_gb300.guide import GuidePass
     return GuidePass(par.width, par.height, spp=par.spp, gamma_dtype=gamma_dtype, seed=par.seed,
                      k_max=par.k_max, pi_min=par.pi_min, pi_max=par.pi_max, pi_reinit=par.pi_reinit,
                      depth_tol=par.depth_tol, normal_tol=par.normal_tol, rough_min=par.rough_min,
                      sigma2_min=par.sigma2_min, rho_max=par.rho_max, init_mu=par.init_mu,
                      init_sigma=par.init_sigma, init_pi=par.init_pi, reuse_radius=par.reuse_radius,
-                     ggx_f0=par.ggx_f0, transparent=par.transparent)
+                     ggx_f0=par.ggx_f0, transparent=par.transparent, **kw)
 
 
 def set_gamma_rows(gp, rows):

@@ -56,7 +56,7 @@ def test_config_default_and_validation_without_gpu(lib):
     for field, bad in (("width", 0), ("height", 32769), ("spp", 0), ("spp", 1025), ("gamma_dtype", 7),
                        ("pi_min", 0.99), ("rho_max", 1.0), ("sigma2_min", 0.0), ("reuse_radius", 9),
                        ("reuse_radius", -1), ("stochastic_round", 2), ("ggx_f0", 1.5), ("ggx_f0", -0.1),
-                       ("transparent", 2)):
+                       ("transparent", 2), ("adam_dtype", 1), ("adam_dtype", 3)):
         c2 = _lib.pg_config()
         C.memmove(C.byref(c2), C.byref(cfg), C.sizeof(cfg))
         setattr(c2, field, bad)
@@ -68,5 +68,7 @@ def test_config_default_and_validation_without_gpu(lib):
     assert lib.pg_reproject(None, None, None, None) == _lib.PG_ERR_ARG
     assert lib.pg_frames_host(None, 1, None, None, None, None, 0, None, None) == _lib.PG_ERR_ARG
     assert lib.pg_check(None) == _lib.PG_ERR_ARG
+    assert lib.pg_get_adam_state(None, None, None) == _lib.PG_ERR_ARG
+    assert lib.pg_set_adam_state(None, None, None) == _lib.PG_ERR_ARG
     assert lib.pg_gamma_bytes(None) == 0
     lib.pg_destroy(None)
