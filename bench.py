@@ -52,7 +52,7 @@ def kernel_counters():
     src = os.path.join(ROOT, "paper_2112_09728_gb300", "csrc")
     try:
         h = hashlib.sha256()
-        for f in ("pg_device.cuh", "pg_kernels.cu", "pg_launch.h"):
+        for f in ("pg_device.cuh", "pg_common.cuh", "pg_kernels.cu"):
             with open(os.path.join(src, f), "rb") as fh:
                 h.update(fh.read())
         sha, traffic, inst = None, None, None
