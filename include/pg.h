@@ -47,7 +47,9 @@ typedef enum {
     PG_ERR_OOM = 3,      /* device allocation failed */
     PG_ERR_STATE = 4,    /* call out of order (e.g. pg_update without pg_reproject) */
     PG_ERR_TIMEOUT = 5,  /* reserved for bounded device waits; no call waits today */
-    PG_ERR_NUMERIC = 6   /* the device flagged a non-finite Gamma (pg_check) */
+    PG_ERR_NUMERIC = 6,  /* the device flagged a non-finite Gamma (pg_check) */
+    PG_ERR_BOUNDS = 7    /* bounds-checked build only (libpg_bounds.so): an index that depends on
+                            the data fell outside its buffer; the access was skipped (pg_check) */
 } pg_status;
 
 /* Storage type of Gamma. PG_F32 stores the paper's raw moments
@@ -356,7 +358,10 @@ pg_status pg_gamma_from_f32(pg_ctx *ctx, const float *d_src);
 pg_status pg_get_reprojected(pg_ctx *ctx, float *d_dst);
 
 /* Wait for the stream and read the device error flag: PG_ERR_NUMERIC if a
- * kernel stored a non-finite Gamma since the last check. */
+ * kernel stored a non-finite Gamma since the last check; in the
+ * bounds-checked build (libpg_bounds.so, compiled with PG_BOUNDS_CHECK),
+ * PG_ERR_BOUNDS if an index that depends on the data (the reprojected pixel,
+ * a reused neighbour's sample) fell outside its buffer. The flag is cleared. */
 pg_status pg_check(pg_ctx *ctx);
 
 /* Philox4x32-10 (Salmon et al., SC'11), the counter-based generator behind

@@ -10,11 +10,12 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libpg.so")
+LIB_BOUNDS_PATH = os.path.join(HERE, "_lib", "libpg_bounds.so")
 
-PG_OK, PG_ERR_ARG, PG_ERR_CUDA, PG_ERR_OOM, PG_ERR_STATE, PG_ERR_TIMEOUT, PG_ERR_NUMERIC = range(7)
+PG_OK, PG_ERR_ARG, PG_ERR_CUDA, PG_ERR_OOM, PG_ERR_STATE, PG_ERR_TIMEOUT, PG_ERR_NUMERIC, PG_ERR_BOUNDS = range(8)
 PG_F32, PG_F16, PG_BF16 = 0, 1, 2
 STATUS_NAMES = {0: "PG_OK", 1: "PG_ERR_ARG", 2: "PG_ERR_CUDA", 3: "PG_ERR_OOM", 4: "PG_ERR_STATE",
-                5: "PG_ERR_TIMEOUT", 6: "PG_ERR_NUMERIC"}
+                5: "PG_ERR_TIMEOUT", 6: "PG_ERR_NUMERIC", 7: "PG_ERR_BOUNDS"}
 
 
 class pg_config(C.Structure):
@@ -84,26 +85,27 @@ _SIGNATURES = {
     "pg_destroy": (None, [_P]),
 }
 
-_lib = None
+_libs = {}
 
 
 def exported_names():
     return list(_SIGNATURES)
 
 
-def load():
-    """Load libpg.so (built in-tree by __graft_entry__.build())."""
-    global _lib
-    if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libpg.so is not built (%s); run __graft_entry__.build() first" % LIB_PATH)
-        lib = C.CDLL(LIB_PATH)
+def load(bounds_check: bool = False):
+    """Load libpg.so, or with bounds_check its bounds-checked build
+    libpg_bounds.so (both built in-tree by __graft_entry__.build())."""
+    path = LIB_BOUNDS_PATH if bounds_check else LIB_PATH
+    if path not in _libs:
+        if not os.path.exists(path):
+            raise RuntimeError("%s is not built; run __graft_entry__.build() first" % path)
+        lib = C.CDLL(path)
         for name, (res, args) in _SIGNATURES.items():
             f = getattr(lib, name)
             f.restype = res
             f.argtypes = args
-        _lib = lib
-    return _lib
+        _libs[path] = lib
+    return _libs[path]
 
 
 class PgError(RuntimeError):

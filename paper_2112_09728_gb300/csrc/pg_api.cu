@@ -203,7 +203,8 @@ pg_status pg_reproject(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev,
     pgk::Params P = c->base;
     if ((s = fill_camera(c, cur->camera, P)) != PG_OK) return s;
     cudaError_t e = pgk::launch_reproject(c->cfg.gamma_dtype, P, c->gam[c->cur], c->work, (const float4*)cur->g0,
-                                          (const float4*)cur->g1, (const float4*)d_g0_prev, d_accept, c->stream);
+                                          (const float4*)cur->g1, (const float4*)d_g0_prev, d_accept, c->d_err,
+                                          c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pg_reproject");
     c->phase = 1;
     c->sample_frame = 0;
@@ -267,7 +268,7 @@ pg_status frame_impl(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, c
     if (c->cfg.reuse_radius > 0) {
         // the paper's two passes: path tracing writes the VPLs, training reads them
         e = pgk::launch_pt(c->cfg.gamma_dtype, P, c->gam[c->cur], g0, g1, g0p, d_img, frame, c->vpl, c->vpl_pb,
-                           c->zbuf, c->stream);
+                           c->zbuf, c->d_err, c->stream);
         if (e == cudaSuccess)
             e = pgk::launch_train(c->cfg.gamma_dtype, P, c->gam[c->cur], c->gam[c->cur ^ 1], g0, g1, g0p, frame,
                                   c->vpl, c->vpl_pb, c->zbuf, c->d_err, c->stream);
@@ -426,6 +427,8 @@ pg_status pg_check(pg_ctx* c) {
     if (e != cudaSuccess) return cuda_fail(c, e, "pg_check");
     if (flag) {
         cudaMemset(c->d_err, 0, sizeof(int));
+        if (flag & PG_ERR_BIT_BOUNDS)
+            return fail(c, PG_ERR_BOUNDS, "an index of the bounds-checked build fell outside its buffer");
         return fail(c, PG_ERR_NUMERIC, "a kernel stored a non-finite Gamma");
     }
     return PG_OK;

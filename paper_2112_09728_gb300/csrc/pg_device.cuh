@@ -20,6 +20,24 @@ constexpr float k4OverPi = 1.27323954473516268615f;
 constexpr int kGLTotal = 4 + 6 + 8;
 
 enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
+
+// Index checks of the debug build (compiled with PG_BOUNDS_CHECK): an index
+// that depends on the data (the reprojected pixel, a reused neighbour's
+// sample) and falls outside its buffer sets bit 2 of the context's error word
+// (pg_check reports PG_ERR_BOUNDS) and the access is skipped. In the normal
+// build the check is the constant true and costs nothing.
+#define PG_ERR_BIT_NUMERIC 1
+#define PG_ERR_BIT_BOUNDS 2
+#ifdef PG_BOUNDS_CHECK
+__device__ __forceinline__ bool pg_in_bounds(long long i, long long n, int* err) {
+    if (i >= 0 && i < n) return true;
+    if (err) atomicOr(err, PG_ERR_BIT_BOUNDS);
+    return false;
+}
+#define PG_IN_BOUNDS(i, n, err) pg_in_bounds((long long)(i), (long long)(n), (err))
+#else
+#define PG_IN_BOUNDS(i, n, err) true
+#endif
 enum { ST_BRDF = 0, ST_GUIDE = 1, ST_FALLBACK = 2, ST_DELTA = 3, ST_INVALID = 4 };
 
 // Everything a launch needs besides its pointers; passed by value (kernel
@@ -389,12 +407,13 @@ __device__ __forceinline__ bool gam_finite(const Gam& g) {
 // Returns the linear index of the previous pixel, or -1 for a rejection.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int reproject_index(const Params& P, int x, int y, float4 g0, float4 g1,
-                                               const float4* __restrict__ g0_prev, float4* g0p_out) {
+                                               const float4* __restrict__ g0_prev, float4* g0p_out, int* err) {
     const float fx = __fadd_rn(__fadd_rn((float)x, 0.5f), g1.x);
     const float fy = __fadd_rn(__fadd_rn((float)y, 0.5f), g1.y);
     if (!(fx >= 0.0f && fx < (float)P.W && fy >= 0.0f && fy < (float)P.H)) return -1;
     const int qx = (int)floorf(fx), qy = (int)floorf(fy);
     const int j = qy * P.W + qx;
+    if (!PG_IN_BOUNDS(j, (long long)P.W * P.H, err)) return -1;
     const float4 gp = __ldcs(g0_prev + j);
     *g0p_out = gp;
     const float dd = fabsf(__fsub_rn(gp.w, g0.w));

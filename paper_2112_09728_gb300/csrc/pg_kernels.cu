@@ -31,9 +31,9 @@ __global__ void __launch_bounds__(kBlock) k_init(const Params P, void* __restric
 template <int DT>
 __device__ __forceinline__ bool reproject_pixel(const Params& P, int x, int y, float4 a0, float4 a1,
                                                 const void* __restrict__ gin, const float4* __restrict__ g0p,
-                                                size_t hw, Gam& g) {
+                                                size_t hw, Gam& g, int* err) {
     float4 gp;
-    const int j = reproject_index(P, x, y, a0, a1, g0p, &gp);
+    const int j = reproject_index(P, x, y, a0, a1, g0p, &gp, err);
     if (j < 0) {
         g = init_gam(P);
         return true;
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void*
     const int y = i / P.W, x = i - y * P.W;
     const float4 a0 = __ldcs(g0 + i), a1 = __ldcs(g1 + i);
     Gam g;
-    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g);
+    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g, err);
     const Surf s = make_surf<GLASS>(P, x, y, a0, a1);
     const Guide d = derive_guide(P, g, gated(P, reinit, a1));
     Stats st;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void*
         st.add_train(d, g, o);
     }
     m_step(P, g, st);
-    if (!gam_finite(g)) atomicOr(err, 1);
+    if (!gam_finite(g)) atomicOr(err, PG_ERR_BIT_NUMERIC);
     store_step<DT>(P, gout, hw, (size_t)i, g, frame);
     if (img) {
         if (RGB) {
@@ -108,14 +108,15 @@ __global__ void __launch_bounds__(kBlock, 5) k_pt(const Params P, const void* __
                                                   const float4* __restrict__ g0, const float4* __restrict__ g1,
                                                   const float4* __restrict__ g0p, float* __restrict__ img,
                                                   uint32_t frame, float4* __restrict__ vpl,
-                                                  float* __restrict__ pb_src, float* __restrict__ zbuf) {
+                                                  float* __restrict__ pb_src, float* __restrict__ zbuf,
+                                                  int* __restrict__ err) {
     const size_t hw = (size_t)P.W * P.H;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if ((size_t)i >= hw) return;
     const int y = i / P.W, x = i - y * P.W;
     const float4 a0 = __ldcs(g0 + i), a1 = __ldcs(g1 + i);
     Gam g;
-    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g);
+    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g, err);
     const Surf s = make_surf(P, x, y, a0, a1);
     const Guide d = derive_guide(P, g, gated(P, reinit, a1));
     zbuf[i] = d.Z;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
     const int y = i / P.W, x = i - y * P.W;
     const float4 a0 = __ldcs(g0 + i), a1 = __ldcs(g1 + i);
     Gam g;
-    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g);
+    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g, err);
     const Surf s = make_surf(P, x, y, a0, a1);
     Guide d = derive_guide_shape(P, g, gated(P, reinit, a1));
     d.Z = __ldcs(zbuf + i);
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
                 q = (size_t)sj * hw + (size_t)qy * P.W + qx;
             }
             ++j;
+            if (!PG_IN_BOUNDS(q, (size_t)spp * hw, err)) continue;
             pb = pb_src[q];
             if (pb > 0.0f) break;
         }
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
         st.add_vpl(d, g, s, make_float3(v.x, v.y, v.z), v.w, pb, P.f0);
     }
     m_step(P, g, st);
-    if (!gam_finite(g)) atomicOr(err, 1);
+    if (!gam_finite(g)) atomicOr(err, PG_ERR_BIT_NUMERIC);
     store_step<DT>(P, gout, hw, (size_t)i, g, frame);
 }
 
@@ -231,14 +233,15 @@ template <int DT>
 __global__ void __launch_bounds__(kBlock) k_reproject(const Params P, const void* __restrict__ gin,
                                                       float4* __restrict__ work, const float4* __restrict__ g0,
                                                       const float4* __restrict__ g1,
-                                                      const float4* __restrict__ g0p, uint8_t* __restrict__ accept) {
+                                                      const float4* __restrict__ g0p, uint8_t* __restrict__ accept,
+                                                      int* __restrict__ err) {
     const size_t hw = (size_t)P.W * P.H;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if ((size_t)i >= hw) return;
     const int y = i / P.W, x = i - y * P.W;
     const float4 a0 = g0[i], a1 = g1[i];
     Gam g;
-    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g);
+    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g, err);
     if (reinit) g.k = -1.0f;  // marks "fresh history, BRDF only" for the next stages
     Work<DT>::store(work, hw, (size_t)i, g);
     if (accept) accept[i] = reinit ? 0 : 1;
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(kBlock) k_update(const Params P, const float4*
         st.add_train(d, g, o);
     }
     m_step(P, g, st);
-    if (!gam_finite(g)) atomicOr(err, 1);
+    if (!gam_finite(g)) atomicOr(err, PG_ERR_BIT_NUMERIC);
     store_step<DT>(P, gout, hw, (size_t)i, g, P.sr_frame);
 }
 
@@ -433,11 +436,11 @@ cudaError_t launch_frame(int dt, const Params& P, const void* gin, void* gout, c
 }
 
 cudaError_t launch_pt(int dt, const Params& P, const void* gin, const float4* g0, const float4* g1,
-                      const float4* g0p, float* img, uint32_t frame, float4* vpl, float* pb_src, float* zbuf,
+                      const float4* g0p, float* img, uint32_t frame, float4* vpl, float* pb_src, float* zbuf, int* err,
                       cudaStream_t st) {
     const dim3 grid = grid_for(P);
 #define PG_PT(ONE, RGB) \
-    PG_DISPATCH(dt, (k_pt<D, ONE, RGB><<<grid, kBlock, 0, st>>>(P, gin, g0, g1, g0p, img, frame, vpl, pb_src, zbuf)))
+    PG_DISPATCH(dt, (k_pt<D, ONE, RGB><<<grid, kBlock, 0, st>>>(P, gin, g0, g1, g0p, img, frame, vpl, pb_src, zbuf, err)))
     if (P.spp == 1 && P.rgb) {
         PG_PT(true, true);
     } else if (P.spp == 1) {
@@ -465,8 +468,8 @@ cudaError_t launch_train(int dt, const Params& P, const void* gin, void* gout, c
 }
 
 cudaError_t launch_reproject(int dt, const Params& P, const void* gin, float4* work, const float4* g0,
-                             const float4* g1, const float4* g0p, uint8_t* accept, cudaStream_t st) {
-    PG_DISPATCH(dt, (k_reproject<D><<<grid_for(P), kBlock, 0, st>>>(P, gin, work, g0, g1, g0p, accept)));
+                             const float4* g1, const float4* g0p, uint8_t* accept, int* err, cudaStream_t st) {
+    PG_DISPATCH(dt, (k_reproject<D><<<grid_for(P), kBlock, 0, st>>>(P, gin, work, g0, g1, g0p, accept, err)));
     return cudaGetLastError();
 }
 

@@ -22,12 +22,12 @@ cudaError_t launch_frame(int dt, const Params& P, const void* gin, void* gout, c
 // neighbour-VPL reuse: the path-tracing pass (writes the VPL buffer) and the training pass
 cudaError_t launch_pt(int dt, const Params& P, const void* gin, const float4* g0, const float4* g1,
                       const float4* g0p, float* img, uint32_t frame, float4* vpl, float* pb_src, float* zbuf,
-                      cudaStream_t st);
+                      int* err, cudaStream_t st);
 cudaError_t launch_train(int dt, const Params& P, const void* gin, void* gout, const float4* g0, const float4* g1,
                          const float4* g0p, uint32_t frame, const float4* vpl, const float* pb_src, const float* zbuf,
                          int* err, cudaStream_t st);
 cudaError_t launch_reproject(int dt, const Params& P, const void* gin, float4* work, const float4* g0,
-                             const float4* g1, const float4* g0p, uint8_t* accept, cudaStream_t st);
+                             const float4* g1, const float4* g0p, uint8_t* accept, int* err, cudaStream_t st);
 cudaError_t launch_sample(int dt, const Params& P, const float4* work, const float4* g0, const float4* g1,
                           uint32_t frame, SamplePlanes out, float* img, cudaStream_t st);
 cudaError_t launch_update(int dt, const Params& P, const float4* work, const float4* g0, const float4* g1,

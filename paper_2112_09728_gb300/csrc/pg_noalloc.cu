@@ -103,7 +103,7 @@ extern "C" pg_status pg_frame_noalloc(const pg_config* cfg, const pg_gbuffer* cu
     // the flag word keeps the previous call's value: clear it first
     if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return PG_ERR_CUDA;
     if (pgk::launch_reproject(dt, P, d_gamma_in, work, g0, g1, reinterpret_cast<const float4*>(d_g0_prev), nullptr,
-                              st) != cudaSuccess)
+                              flag, st) != cudaSuccess)
         return PG_ERR_CUDA;
     if (pgk::launch_sample(dt, P, work, g0, g1, frame, s, d_img, st) != cudaSuccess) return PG_ERR_CUDA;
     P.sr_frame = frame;

@@ -75,7 +75,7 @@ def alloc_samples(spp, hw, device="cuda"):
 def make_config(width, height, spp=1, gamma_dtype="f32", seed=0, **overrides) -> L.pg_config:
     """pg_config with the library's defaults and the given overrides."""
     cfg = L.pg_config()
-    L.load().pg_config_default(C.byref(cfg), int(width), int(height))
+    L.load(overrides.pop("bounds_check", False)).pg_config_default(C.byref(cfg), int(width), int(height))
     cfg.spp = int(spp)
     cfg.gamma_dtype = _DTYPES[gamma_dtype]
     cfg.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
@@ -94,9 +94,12 @@ def make_config(width, height, spp=1, gamma_dtype="f32", seed=0, **overrides) ->
 class GuidePass:
     """One guide-pass context (pg_ctx): owns Gamma on the current device."""
 
-    def __init__(self, width, height, spp=1, gamma_dtype="f32", seed=0, **overrides):
-        self._lib = L.load()
-        cfg = make_config(width, height, spp, gamma_dtype, seed, **overrides)
+    def __init__(self, width, height, spp=1, gamma_dtype="f32", seed=0, bounds_check=False, **overrides):
+        """bounds_check: run on the bounds-checked build of the library
+        (libpg_bounds.so), whose pg_check reports PG_ERR_BOUNDS for an index
+        outside its buffer."""
+        self._lib = L.load(bounds_check)
+        cfg = make_config(width, height, spp, gamma_dtype, seed, bounds_check=bounds_check, **overrides)
         self.cfg = cfg
         self.width, self.height, self.spp = int(width), int(height), int(spp)
         self.hw = self.width * self.height

@@ -37,6 +37,31 @@ def test_header_declares_the_boundary():
 def test_every_declared_symbol_is_exported(lib):
     missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
     assert not missing, missing
+    from paper_2112_09728_gb300 import _lib
+    checked = _lib.load(bounds_check=True)          # the bounds-checked build exports the same ABI
+    missing = [n for n in sorted(_declared()) if not hasattr(checked, n)]
+    assert not missing, missing
+
+
+def test_reuse_pick_decode_is_exact_in_binary32():
+    """The training pass decodes candidate o of the (2R+1)^2 - 1 window cells
+    x spp samples with binary32 floor divisions, cell = floor((o + 0.5) *
+    fl(1/spp)) and row = floor((cell + 0.5) * fl(1/(2R+1))), to avoid integer
+    division. Both equal the integer quotients for every candidate of every
+    configuration the library accepts (spp <= 1024, R <= 8)."""
+    import numpy as np
+    f32 = np.float32
+    for spp in range(2, 1025):
+        c = (17 * 17 - 1) * spp                     # the largest window; smaller ones are prefixes
+        o = np.arange(c, dtype=np.int64)
+        inv = f32(1) / f32(spp)
+        cell = ((o.astype(f32) + f32(0.5)) * inv).astype(np.int64)     # truncation of a positive value
+        assert np.array_equal(cell, o // spp), spp
+    for r in range(1, 9):
+        d = 2 * r + 1
+        cell = np.arange(d * d, dtype=np.int64)
+        row = ((cell.astype(f32) + f32(0.5)) * (f32(1) / f32(d))).astype(np.int64)
+        assert np.array_equal(row, cell // d), r
 
 
 def test_binding_covers_every_declared_symbol(lib):
