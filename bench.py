@@ -215,6 +215,40 @@ def oracle_strip_frames(rows, budget_s, min_steps=1, max_steps=1000, frame_base=
     return px, sec, steps
 
 
+def oracle_field(O, fld):
+    """The oracle's field of a scenes.Field (parameters rounded to binary32,
+    as the library receives them)."""
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    return O.make_field(f32(fld.dirs), f32(fld.kappas), f32(fld.amps), float(np.float32(fld.constant)),
+                        None if fld.mask is None else [float(np.float32(m)) for m in fld.mask])
+
+
+def oracle_4k_pixels(par, fld, sc, frame, budget_s, batch=1000):
+    """The FP64 oracle on random pixels of one frame of the 3840x2160 orbit
+    workload (4 spp, 8 lobes), each computed alone from the initial guide,
+    until budget_s seconds of work; returns the cpu_baseline object."""
+    import oracle as O
+    g0, g1, g0p = (a.cpu().numpy() for a in sc.gbuffer_on(frame, "cuda"))
+    cfg = O.make_config(par.width, par.height, spp=par.spp, seed=par.seed, init_mu=par.init_mu,
+                        init_sigma=par.init_sigma)
+    row = O.init_gamma(cfg, 1, pi=par.init_pi)[0]
+    cam = sc.camera(frame)
+    oc = O.make_camera(cam.kind, cam.origin, cam.fwd, cam.right, cam.up, cam.pixel_size, cam.tan_half_fov)
+    of = oracle_field(O, fld)
+    rng = np.random.default_rng(4)
+    px, sec = 0, 0.0
+    while sec < budget_s or px == 0:
+        xs = rng.integers(0, par.width, batch)
+        ys = rng.integers(0, par.height, batch)
+        t0 = time.perf_counter()
+        O.frame_pixels(cfg, oc, of, frame, g0, g1, g0p, row, xs, ys)
+        sec += time.perf_counter() - t0
+        px += batch
+    return {"value": px / sec / 1e6, "unit": "Mpix/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": "%d random pixels of frame %d of the 3840x2160 orbit workload (4 spp, 8 lobes), each "
+                      "computed alone from the initial guide" % (px, frame)}
+
+
 def cpu_cores():
     n = os.environ.get("OMP_NUM_THREADS")
     return int(n) if n else (os.cpu_count() or 1)
@@ -662,6 +696,8 @@ def run_gpu(args, ws, rank, local):
     if not args.no_4k:
         wl4 = scenes.workload_4k()
         w4k = run_4k(wl4["params"], wl4["field"], wl4["scene"], 4, 8, flush)
+        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+            w4k["cpu_baseline"] = oracle_4k_pixels(wl4["params"], wl4["field"], wl4["scene"], 4, args.cpu_budget / 2)
     diff = None if args.no_diff else run_diff()
     temporal = None if args.no_temporal else run_temporal()
     rounding = None if args.no_temporal else run_rounding()
