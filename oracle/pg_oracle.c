@@ -122,8 +122,8 @@ static double unif(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }
 static double unif_open0(uint32_t w) { return (double)((w >> 8) + 1u) * (1.0 / 16777216.0); }
 
 /* ------------------------------------------------------------------------ */
-/* Shirley-Chiu concentric map M (Eq. 2, "Shirley and Chiu area preserving  */
-/* mapping"): unit square -> unit disk by concentric squares, then the      */
+/* Shirley-Chiu concentric map M (Eq. 2: the area-preserving map of        */
+/* Shirley and Chiu): unit square -> unit disk by concentric squares, the   */
 /* equal-area lift of the disk to the hemisphere, so dw = 2*pi du dv.       */
 /* Pinned by: round trip, constant Jacobian 2*pi, boundary -> horizon,      */
 /* centre -> pole, moments of the uniform hemisphere.                       */

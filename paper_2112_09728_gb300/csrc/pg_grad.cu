@@ -10,7 +10,7 @@ namespace {
 // ---------------------------------------------------------------------------
 // The differentiable form: the gradient of the per-pixel second-moment loss
 // l(theta) = 1/n sum f_i^2 / (p_theta(w_i) p_theta0(w_i)) at theta = theta0,
-// with the n directions drawn from the guide itself (Philox streams 2 and 3):
+// with the n directions drawn from the guide itself (Philox stream 2):
 //   l = 1/n sum f^2 / p^2,  dl/dtheta = -1/n sum f^2 (dp/dtheta) / p^3,
 //   dp/dpi = g - Z p_b,  dp/dmu = pi (g Sigma^-1 d - p_b dZ/dmu),
 //   dp/dSigma = pi (g/2 (Sigma^-1 d d^T Sigma^-1 - Sigma^-1) - p_b dZ/dSigma)
