@@ -19,7 +19,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libpg.so")
 LIB_BOUNDS = os.path.join(OUT, "libpg_bounds.so")
-SOURCES = ["pg_kernels.cu", "pg_grad.cu", "pg_api.cu", "pg_params.cu", "pg_noalloc.cu"]
+SOURCES = ["pg_kernels.cu", "pg_reuse.cu", "pg_grad.cu", "pg_api.cu", "pg_params.cu", "pg_noalloc.cu"]
 HEADERS = ["pg_device.cuh", "pg_common.cuh", "pg_launch.h", "pg_params.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

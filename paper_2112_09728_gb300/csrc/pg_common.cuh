@@ -20,6 +20,23 @@ static __device__ __forceinline__ bool gated(const Params& P, bool reinit, float
     return reinit || (g1.z >= 0.0f && g1.z < P.rough_min) || (P.glass && g1.z <= -1.5f);
 }
 
+// Reprojection of one pixel: Gamma(t-1) at the motion-compensated pixel, or a
+// re-initialised guide. Returns true for a re-initialised pixel.
+template <int DT>
+static __device__ __forceinline__ bool reproject_pixel(const Params& P, int x, int y, float4 a0, float4 a1,
+                                                const void* __restrict__ gin, const float4* __restrict__ g0p,
+                                                size_t hw, Gam& g, int* err) {
+    float4 gp;
+    const int j = reproject_index(P, x, y, a0, a1, g0p, &gp, err);
+    if (j < 0) {
+        g = init_gam(P);
+        return true;
+    }
+    g = Store<DT>::load(gin, hw, (size_t)j);
+    if (!same_normal(gp, a0)) change_frame(g, make_float3(gp.x, gp.y, gp.z), make_float3(a0.x, a0.y, a0.z));
+    return false;
+}
+
 static inline dim3 grid_for(const Params& P) {
     const size_t hw = (size_t)P.W * P.H;
     return dim3((unsigned)((hw + kBlock - 1) / kBlock));

@@ -1,0 +1,177 @@
+// Neighbour-VPL reuse (Sec. 3.2, 4.2): the frame as the paper's two passes.
+// k_pt reprojects, samples and writes one VPL per sample (world direction,
+// radiance and, for a BRDF-strategy draw, its BRDF density) plus Z per pixel;
+// k_train reprojects again and trains each pixel's guide on its own samples
+// and N picks among its window's samples.
+#include "pg_common.cuh"
+
+namespace pgk {
+
+namespace {
+
+// Neighbour-VPL reuse, pass 1 (path tracing, Fig. 2): the frame's samples
+// and image as in k_frame, plus one VPL per sample in the buffer Pi: world
+// direction and radiance in vpl, and in pb_src the density of the pixel's
+// BRDF draw for a BRDF-strategy sample (0 for samples that do not train).
+// The guide's rectangle mass Z goes to zbuf for the training pass.
+template <int DT, bool ONE, bool RGB>
+__global__ void __launch_bounds__(kBlock, 5) k_pt(const Params P, const void* __restrict__ gin,
+                                                  const float4* __restrict__ g0, const float4* __restrict__ g1,
+                                                  const float4* __restrict__ g0p, float* __restrict__ img,
+                                                  uint32_t frame, float4* __restrict__ vpl,
+                                                  float* __restrict__ pb_src, float* __restrict__ zbuf,
+                                                  int* __restrict__ err) {
+    const size_t hw = (size_t)P.W * P.H;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((size_t)i >= hw) return;
+    const int y = i / P.W, x = i - y * P.W;
+    const float4 a0 = __ldcs(g0 + i), a1 = __ldcs(g1 + i);
+    Gam g;
+    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g, err);
+    const Surf s = make_surf(P, x, y, a0, a1);
+    const Guide d = derive_guide(P, g, gated(P, reinit, a1));
+    zbuf[i] = d.Z;
+    Kahan f, fr, fg, fb;
+    const int spp = ONE ? 1 : P.spp;
+    for (int si = 0; si < spp; ++si) {
+        const Smp o = draw_sample<RGB>(P, d, s, (uint32_t)i, frame, (uint32_t)si);
+        if (si == 0) {
+            f.set(o.F);
+            if (RGB) {
+                fr.set(o.wgt * o.Lrgb.x);
+                fg.set(o.wgt * o.Lrgb.y);
+                fb.set(o.wgt * o.Lrgb.z);
+            }
+        } else {
+            f.add(o.F);
+            if (RGB) {
+                fr.add(o.wgt * o.Lrgb.x);
+                fg.add(o.wgt * o.Lrgb.y);
+                fb.add(o.wgt * o.Lrgb.z);
+            }
+        }
+        const float3 ww = to_world(s.f, o.wl);
+        const size_t q = (size_t)si * hw + i;
+        vpl[q] = make_float4(ww.x, ww.y, ww.z, o.L);
+        pb_src[q] = (o.strat == ST_BRDF && o.pb > 0.0f) ? o.pb : 0.0f;
+    }
+    if (img) {
+        if (RGB) {
+            __stcs(img + i, ONE ? fr.s : fdiv(fr.s, (float)spp));
+            __stcs(img + hw + i, ONE ? fg.s : fdiv(fg.s, (float)spp));
+            __stcs(img + 2 * hw + i, ONE ? fb.s : fdiv(fb.s, (float)spp));
+        } else {
+            __stcs(img + i, ONE ? f.s : fdiv(f.s, (float)spp));
+        }
+    }
+}
+
+// Neighbour-VPL reuse, pass 2 (training, Sec. 3.2 and 4.2): the pixel's own
+// BRDF-strategy VPLs and N picks of its window, each weighted f / p_src, then
+// the M-step. N = 5 + floor(15 (k_max - k) / k_max) (at most the window's C
+// candidates); the picks walk the candidates from a Philox start by a stride
+// coprime with C, so they are distinct. Reprojection is recomputed (same
+// inputs, same result as pass 1) rather than stored; Z comes from pass 1.
+//
+// Each thread walks its own picks to the next one that trains (inside the
+// image, drawn by the BRDF strategy) before the warp evaluates a VPL, so a
+// warp runs as many evaluations as its busiest lane has training VPLs, not
+// one per pick.
+template <int DT, bool ONE>
+__global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void* __restrict__ gin,
+                                                     void* __restrict__ gout, const float4* __restrict__ g0,
+                                                     const float4* __restrict__ g1,
+                                                     const float4* __restrict__ g0p, uint32_t frame,
+                                                     const float4* __restrict__ vpl,
+                                                     const float* __restrict__ pb_src,
+                                                     const float* __restrict__ zbuf, int* __restrict__ err) {
+    const size_t hw = (size_t)P.W * P.H;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((size_t)i >= hw) return;
+    const int y = i / P.W, x = i - y * P.W;
+    const float4 a0 = __ldcs(g0 + i), a1 = __ldcs(g1 + i);
+    Gam g;
+    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g, err);
+    const Surf s = make_surf(P, x, y, a0, a1);
+    Guide d = derive_guide_shape(P, g, gated(P, reinit, a1));
+    d.Z = __ldcs(zbuf + i);
+    const int spp = ONE ? 1 : P.spp;
+    const int kc = (int)fminf(fmaxf(g.k, 0.0f), (float)P.k_max);
+    const int n = min(5 + (15 * (P.k_max - kc)) / P.k_max, P.reuse_c);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, frame, 0u, 4u), P.rk);
+    int o = (int)(((uint64_t)r.x * (uint64_t)P.reuse_c) >> 32);
+    const int dw = 2 * P.reuse_r + 1, center = (dw * dw - 1) / 2;
+    int j = -spp;   // own samples first (j < 0), then the picks
+    Stats st;
+    while (true) {
+        // this lane's next VPL that trains
+        float pb = 0.0f;
+        size_t q = 0;
+        while (j < n) {
+            if (j < 0) {
+                q = (size_t)(j + spp) * hw + i;
+            } else {
+                // candidate o: pixel cell o / spp of the window (p itself skipped), sample o mod spp;
+                // the floor divisions are exact in binary32 for these small integers
+                const int cell0 = ONE ? o : (int)(((float)o + 0.5f) * P.reuse_inv_spp);
+                const int sj = o - cell0 * spp;
+                const int cell = cell0 + (cell0 >= center ? 1 : 0);
+                const int ry = (int)(((float)cell + 0.5f) * P.reuse_inv_dw);
+                const int qx = x + cell - ry * dw - P.reuse_r, qy = y + ry - P.reuse_r;
+                o += P.reuse_stride;
+                if (o >= P.reuse_c) o -= P.reuse_c;
+                if (qx < 0 || qx >= P.W || qy < 0 || qy >= P.H) {
+                    ++j;
+                    continue;
+                }
+                q = (size_t)sj * hw + (size_t)qy * P.W + qx;
+            }
+            ++j;
+            if (!PG_IN_BOUNDS(q, (size_t)spp * hw, err)) continue;
+            pb = pb_src[q];
+            if (pb > 0.0f) break;
+        }
+        if (!(pb > 0.0f)) break;
+        const float4 v = vpl[q];
+        st.add_vpl(d, g, s, make_float3(v.x, v.y, v.z), v.w, pb, P.f0);
+    }
+    m_step(P, g, st);
+    if (!gam_finite(g)) atomicOr(err, PG_ERR_BIT_NUMERIC);
+    store_step<DT>(P, gout, hw, (size_t)i, g, frame);
+}
+
+}  // namespace
+
+cudaError_t launch_pt(int dt, const Params& P, const void* gin, const float4* g0, const float4* g1,
+                      const float4* g0p, float* img, uint32_t frame, float4* vpl, float* pb_src, float* zbuf, int* err,
+                      cudaStream_t st) {
+    const dim3 grid = grid_for(P);
+#define PG_PT(ONE, RGB) \
+    PG_DISPATCH(dt, (k_pt<D, ONE, RGB><<<grid, kBlock, 0, st>>>(P, gin, g0, g1, g0p, img, frame, vpl, pb_src, zbuf, err)))
+    if (P.spp == 1 && P.rgb) {
+        PG_PT(true, true);
+    } else if (P.spp == 1) {
+        PG_PT(true, false);
+    } else if (P.rgb) {
+        PG_PT(false, true);
+    } else {
+        PG_PT(false, false);
+    }
+#undef PG_PT
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train(int dt, const Params& P, const void* gin, void* gout, const float4* g0, const float4* g1,
+                         const float4* g0p, uint32_t frame, const float4* vpl, const float* pb_src, const float* zbuf,
+                         int* err, cudaStream_t st) {
+    if (P.spp == 1) {
+        PG_DISPATCH(dt, (k_train<D, true><<<grid_for(P), kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, frame, vpl,
+                                                                          pb_src, zbuf, err)));
+    } else {
+        PG_DISPATCH(dt, (k_train<D, false><<<grid_for(P), kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, frame, vpl,
+                                                                           pb_src, zbuf, err)));
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pgk
