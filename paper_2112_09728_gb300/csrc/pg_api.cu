@@ -79,6 +79,31 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
     return a && b && pa < pb + nb && pb < pa + na;
 }
 
+// Frees the host pipeline's streams, events and device rings (any subset may
+// exist after a failed set-up) and clears the pointers.
+void release_host(pg_ctx* c) {
+    for (int k = 0; k < 3; ++k) {
+        if (c->hg0[k]) cudaFree(c->hg0[k]);
+        c->hg0[k] = nullptr;
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (c->hg1[k]) cudaFree(c->hg1[k]);
+        if (c->himg[k]) cudaFree(c->himg[k]);
+        c->hg1[k] = nullptr;
+        c->himg[k] = nullptr;
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (c->ev_up[k]) cudaEventDestroy(c->ev_up[k]);
+        if (c->ev_ran[k]) cudaEventDestroy(c->ev_ran[k]);
+        if (c->ev_down[k]) cudaEventDestroy(c->ev_down[k]);
+        c->ev_up[k] = c->ev_ran[k] = c->ev_down[k] = nullptr;
+    }
+    if (c->hs_up) cudaStreamDestroy(c->hs_up);
+    if (c->hs_down) cudaStreamDestroy(c->hs_down);
+    c->hs_up = c->hs_down = nullptr;
+    c->host_ready = false;
+}
+
 pg_status ensure_host(pg_ctx* c) {
     if (c->host_ready) return PG_OK;
     const size_t hw = hw_of(c);
@@ -96,6 +121,7 @@ pg_status ensure_host(pg_ctx* c) {
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
+        release_host(c);   // a later call starts from nothing
         return fail(c, PG_ERR_OOM, std::string("pg_frames_host: cannot set up the host pipeline: ") +
                                        cudaGetErrorString(e));
     }
@@ -566,19 +592,9 @@ void pg_destroy(pg_ctx* c) {
     if (c->vpl) cudaFree(c->vpl);
     if (c->vpl_pb) cudaFree(c->vpl_pb);
     if (c->zbuf) cudaFree(c->zbuf);
-    for (int k = 0; k < 3; ++k)
-        if (c->hg0[k]) cudaFree(c->hg0[k]);
-    for (int k = 0; k < 2; ++k) {
-        if (c->hg1[k]) cudaFree(c->hg1[k]);
-        if (c->himg[k]) cudaFree(c->himg[k]);
-    }
-    for (int k = 0; k < 4; ++k) {
-        if (c->ev_up[k]) cudaEventDestroy(c->ev_up[k]);
-        if (c->ev_ran[k]) cudaEventDestroy(c->ev_ran[k]);
-        if (c->ev_down[k]) cudaEventDestroy(c->ev_down[k]);
-    }
-    if (c->hs_up) cudaStreamDestroy(c->hs_up);
-    if (c->hs_down) cudaStreamDestroy(c->hs_down);
+    if (c->hs_up) cudaStreamSynchronize(c->hs_up);
+    if (c->hs_down) cudaStreamSynchronize(c->hs_down);
+    release_host(c);
     delete c;
 }
 
