@@ -244,14 +244,15 @@ def oracle_4k_pixels(par, fld, sc, frame, budget_s, batch=1000):
         O.frame_pixels(cfg, oc, of, frame, g0, g1, g0p, row, xs, ys)
         sec += time.perf_counter() - t0
         px += batch
-    return {"value": px / sec / 1e6, "unit": "Mpix/s", "cores": cpu_cores(), "kind": "oracle",
+    return {"value": px / sec / 1e6, "unit": "Mpix/s", "cores": O.max_threads(), "kind": "oracle",
             "sample": "%d random pixels of frame %d of the 3840x2160 orbit workload (4 spp, 8 lobes), each "
                       "computed alone from the initial guide" % (px, frame)}
 
 
 def cpu_cores():
-    n = os.environ.get("OMP_NUM_THREADS")
-    return int(n) if n else (os.cpu_count() or 1)
+    """Threads the oracle's parallel loops use."""
+    import oracle as O
+    return O.max_threads()
 
 
 def run_reference(args, ws, rank):
@@ -716,9 +717,19 @@ def run_gpu(args, ws, rank, local):
     traffic, inst = kernel_counters()
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
+        import oracle as O
+        threads = O.max_threads()
         px, sec, steps = oracle_strip_frames(16, args.cpu_budget)
-        cpu = {"value": px / sec / 1e6, "unit": "Mpix/s", "cores": cpu_cores(), "kind": "oracle",
+        cpu = {"value": px / sec / 1e6, "unit": "Mpix/s", "cores": threads, "kind": "oracle",
                "sample": "%d frames of a 1920x16 strip of the workload (frames 1..%d)" % (steps, steps)}
+        # the same oracle on one thread, on 1920x2 strips
+        O.set_threads(1)
+        try:
+            px1, sec1, steps1 = oracle_strip_frames(2, args.cpu_budget / 4)
+        finally:
+            O.set_threads(threads)
+        cpu["single_thread"] = {"value": px1 / sec1 / 1e6, "unit": "Mpix/s", "cores": 1,
+                                "sample": "%d frames of a 1920x2 strip of the workload" % steps1}
     line = {
         "metric": METRIC, "value": main["mpix_s"], "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",

@@ -103,6 +103,8 @@ def _load():
                 "or_frame_pixels": [_P, _P, _P, C.c_uint32, _P, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P],
                 "or_brdf_cos_f0": [C.c_double, C.c_double, C.c_double, _P, _P],
                 "or_dielectric_fresnel": [C.c_double],
+                "or_set_threads": [C.c_int],
+                "or_max_threads": [],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -117,8 +119,18 @@ def _load():
             lib.or_reuse_picks.restype = C.c_int
             lib.or_brdf_cos_f0.restype = C.c_double
             lib.or_dielectric_fresnel.restype = C.c_double
+            lib.or_max_threads.restype = C.c_int
             _lib = lib
     return _lib
+
+
+def set_threads(n):
+    """Threads of the oracle's parallel loops (for timing; results do not depend on it)."""
+    _load().or_set_threads(int(n))
+
+
+def max_threads():
+    return int(_load().or_max_threads())
 
 
 def _ptr(a):

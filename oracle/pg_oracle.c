@@ -23,6 +23,7 @@
  * "parity unpinned").
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1380,3 +1381,9 @@ void or_adam(const or_config *cfg, int64_t n, double *gam, const double *grad, d
         gm[G_K] = k; gm[G_W] = wmass;
     }
 }
+
+/* Threads of the oracle's parallel loops (OpenMP): for timing it on a
+ * stated number of host cores. Changes no result: every pixel is computed
+ * alone, in the same order of operations, whatever thread runs it. */
+void or_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int or_max_threads(void) { return omp_get_max_threads(); }
