@@ -73,10 +73,12 @@ __global__ void __launch_bounds__(kBlock, 5) k_pt(const Params P, const void* __
 // coprime with C, so they are distinct. Reprojection is recomputed (same
 // inputs, same result as pass 1) rather than stored; Z comes from pass 1.
 //
-// Each thread walks its own picks to the next one that trains (inside the
-// image, drawn by the BRDF strategy) before the warp evaluates a VPL, so a
-// warp runs as many evaluations as its busiest lane has training VPLs, not
-// one per pick.
+// Each thread first classifies its N picks in a loop of the same length on
+// every lane (decode, on screen, drawn by the BRDF strategy), keeping a bit
+// per training pick, then evaluates only those. A warp thus runs as many
+// evaluations as its busiest lane has training VPLs, with no lane waiting on
+// another's search for its next one. The own samples come first, then the
+// picks in pick order: the order of the compensated sums is the pick order.
 template <int DT, bool ONE>
 __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void* __restrict__ gin,
                                                      void* __restrict__ gout, const float4* __restrict__ g0,
@@ -99,39 +101,46 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
     const int kc = (int)fminf(fmaxf(g.k, 0.0f), (float)P.k_max);
     const int n = min(5 + (15 * (P.k_max - kc)) / P.k_max, P.reuse_c);
     const uint4 r = philox4x32_10(make_uint4((uint32_t)i, frame, 0u, 4u), P.rk);
-    int o = (int)(((uint64_t)r.x * (uint64_t)P.reuse_c) >> 32);
+    const int o0 = (int)(((uint64_t)r.x * (uint64_t)P.reuse_c) >> 32);
     const int dw = 2 * P.reuse_r + 1, center = (dw * dw - 1) / 2;
-    int j = -spp;   // own samples first (j < 0), then the picks
+    // candidate o: pixel cell o / spp of the window (p itself skipped), sample
+    // o mod spp; the floor divisions are exact in binary32 for these small
+    // integers. False for a cell off the screen.
+    auto candidate = [&](int o, size_t& q) {
+        const int cell0 = ONE ? o : (int)(((float)o + 0.5f) * P.reuse_inv_spp);
+        const int sj = o - cell0 * spp;
+        const int cell = cell0 + (cell0 >= center ? 1 : 0);
+        const int ry = (int)(((float)cell + 0.5f) * P.reuse_inv_dw);
+        const int qx = x + cell - ry * dw - P.reuse_r, qy = y + ry - P.reuse_r;
+        if (qx < 0 || qx >= P.W || qy < 0 || qy >= P.H) return false;
+        q = (size_t)sj * hw + (size_t)qy * P.W + qx;
+        return PG_IN_BOUNDS(q, (size_t)spp * hw, err);
+    };
+    // pick j (j < n <= 20) trains iff bit j of mask is set
+    uint32_t mask = 0u;
+    for (int j = 0, o = o0; j < n; ++j) {
+        size_t q;
+        if (candidate(o, q) && pb_src[q] > 0.0f) mask |= 1u << j;
+        o += P.reuse_stride;
+        if (o >= P.reuse_c) o -= P.reuse_c;
+    }
     Stats st;
-    while (true) {
-        // this lane's next VPL that trains
-        float pb = 0.0f;
-        size_t q = 0;
-        while (j < n) {
-            if (j < 0) {
-                q = (size_t)(j + spp) * hw + i;
-            } else {
-                // candidate o: pixel cell o / spp of the window (p itself skipped), sample o mod spp;
-                // the floor divisions are exact in binary32 for these small integers
-                const int cell0 = ONE ? o : (int)(((float)o + 0.5f) * P.reuse_inv_spp);
-                const int sj = o - cell0 * spp;
-                const int cell = cell0 + (cell0 >= center ? 1 : 0);
-                const int ry = (int)(((float)cell + 0.5f) * P.reuse_inv_dw);
-                const int qx = x + cell - ry * dw - P.reuse_r, qy = y + ry - P.reuse_r;
-                o += P.reuse_stride;
-                if (o >= P.reuse_c) o -= P.reuse_c;
-                if (qx < 0 || qx >= P.W || qy < 0 || qy >= P.H) {
-                    ++j;
-                    continue;
-                }
-                q = (size_t)sj * hw + (size_t)qy * P.W + qx;
-            }
-            ++j;
-            if (!PG_IN_BOUNDS(q, (size_t)spp * hw, err)) continue;
-            pb = pb_src[q];
-            if (pb > 0.0f) break;
+    for (int si = 0; si < spp; ++si) {           // the pixel's own samples
+        const size_t q = (size_t)si * hw + i;
+        const float pb = pb_src[q];
+        if (pb > 0.0f) {
+            const float4 v = vpl[q];
+            st.add_vpl(d, g, s, make_float3(v.x, v.y, v.z), v.w, pb, P.f0);
         }
-        if (!(pb > 0.0f)) break;
+    }
+    while (mask) {                               // the training picks, in pick order
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        // o_j = (o_0 + j stride) mod C; below 2^32 since C, stride < 2^19 and j < 20
+        const int o = (int)(((uint32_t)o0 + (uint32_t)j * (uint32_t)P.reuse_stride) % (uint32_t)P.reuse_c);
+        size_t q = 0;
+        candidate(o, q);
+        const float pb = pb_src[q];
         const float4 v = vpl[q];
         st.add_vpl(d, g, s, make_float3(v.x, v.y, v.z), v.w, pb, P.f0);
     }
