@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
     };
     // pick j (j < n <= 20) trains iff bit j of mask is set
     uint32_t mask = 0u;
+#pragma unroll 4
     for (int j = 0, o = o0; j < n; ++j) {
         size_t q;
         if (candidate(o, q) && pb_src[q] > 0.0f) mask |= 1u << j;
