@@ -288,18 +288,19 @@ def upload_frames(sc, n_frames, pin=False):
     return g0, g1
 
 
-def make_pass(par, gamma_dtype, seed_offset=0, spp=1, reuse_radius=0):
+def make_pass(par, gamma_dtype, seed_offset=0, spp=1, reuse_radius=0, **overrides):
     from paper_2112_09728_gb300.guide import GuidePass
     return GuidePass(par.width, par.height, spp=spp, gamma_dtype=gamma_dtype, seed=par.seed + seed_offset,
-                     init_pi=par.init_pi, reuse_radius=reuse_radius)
+                     init_pi=par.init_pi, reuse_radius=reuse_radius, **overrides)
 
 
-def run_form(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush, keep_frames, seed_offset, reuse_radius=0):
+def run_form(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush, keep_frames, seed_offset, reuse_radius=0,
+             **overrides):
     """Run frames 0..warmup+steps-1; time each of the last `steps` with CUDA events
     (L2 flushed before each). Returns (per-step ms list, {frame: image})."""
     import torch
     from paper_2112_09728_gb300.guide import GuidePass
-    gp = make_pass(par, gamma_dtype, seed_offset, reuse_radius=reuse_radius)
+    gp = make_pass(par, gamma_dtype, seed_offset, reuse_radius=reuse_radius, **overrides)
     hw = par.width * par.height
     img = torch.empty(GuidePass.image_planes(fld) * hw, dtype=torch.float32, device="cuda")
     kept = {}
@@ -322,6 +323,20 @@ def run_form(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush, keep_fra
     ms = [a.elapsed_time(b) for a, b in ev]
     gp.close()
     return ms, kept
+
+
+def with_transparent_texels(g1d, sc, frac, seed):
+    """A copy of the frames' G1 planes in which a seeded fraction of the
+    world's texels carry the transparent material code (-2), following the
+    pan, so a texel keeps its material from frame to frame."""
+    import torch
+    rng = np.random.default_rng(seed + 31)
+    world = torch.from_numpy(rng.random((sc.H, sc.W + sc.pan * max(sc.T, 1))) < frac)
+    g1m = g1d.clone()
+    for t in range(g1m.shape[0]):
+        glass = world[:, sc.pan * t:sc.pan * t + sc.W].reshape(-1).to(g1m.device)
+        g1m[t, :, 2] = torch.where(glass, torch.full_like(g1m[t, :, 2], -2.0), g1m[t, :, 2])
+    return g1m
 
 
 def reference_images(par, sc, fld, g0d, g1d, frames):
@@ -675,6 +690,12 @@ def run_gpu(args, ws, rank, local):
     # the same frames with the field's lobes coloured (three image planes)
     rgb_ms = run_form(par, sc, scenes.coloured(fld, 2), g0d, g1d, "f16", args.warmup, args.steps, flush, set(),
                       rank)[0]
+    # the same frames with a tenth of the world's texels transparent and
+    # Schlick's F0 = 0.04 on the GGX ones (the transparent-material kernel)
+    g1m = with_transparent_texels(g1d, sc, 0.1, par.seed)
+    mat_ms = run_form(par, sc, fld, g0d, g1m, "f16", args.warmup, args.steps, flush, set(), rank, transparent=1,
+                      ggx_f0=0.04)[0]
+    del g1m
 
     # matched MSE against a 256-spp reference of frames 30-59
     mse = None
@@ -743,6 +764,10 @@ def run_gpu(args, ws, rank, local):
         "rgb": {"ms_per_step": sum(rgb_ms) / len(rgb_ms), "gamma_storage": "f16",
                 "mpix_s": hw * len(rgb_ms) / sum(rgb_ms) / 1e3, "algorithmic_bytes_per_pixel": 64 + 16 + 12,
                 "field": "the workload's 4 lobes, each with a colour (three image planes)"},
+        "materials": {"ms_per_step": sum(mat_ms) / len(mat_ms), "gamma_storage": "f16",
+                      "mpix_s": hw * len(mat_ms) / sum(mat_ms) / 1e3, "transparent_fraction": 0.1, "ggx_f0": 0.04,
+                      "setting": "a tenth of the world's texels transparent (guiding off, Fresnel-weighted delta "
+                                 "reflection or refraction), Schlick F0 = 0.04 on the GGX texels"},
         "staged": {"ms_per_step": sum(staged_ms) / len(staged_ms), "gamma_storage": "f16", "kernels_per_frame": 3,
                    "fused_speedup": (sum(staged_ms) / len(staged_ms)) / res["f16"]["ms_per_step"]},
         "reuse": {"radius": REUSE_R, "gamma_storage": "f16", "kernels_per_frame": 2,
