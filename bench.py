@@ -782,9 +782,11 @@ def run_gpu(args, ws, rank, local):
                      "issue": issue_roofline(inst, main["ms_per_step"], (clocks or {}).get("sm_mhz"))},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_v, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": sum(e2e_ms) / len(e2e_ms),
+                "h2d_gbs": h2d / (sum(e2e_ms) / len(e2e_ms) * 1e-3) / 1e9,
                 "api": "pg_frames_host (C ABI, host buffers): page-locked G-buffer uploads and image "
                        "read-backs overlapped with the frames on three streams; wall clock of the call, "
-                       "median of three runs"},
+                       "median of three runs; bound by the host-to-device link"},
         "workload_4k": w4k,
         "diff_form": diff,
         "temporal_stability": temporal,
