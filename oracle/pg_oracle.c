@@ -355,6 +355,12 @@ void or_rect_mass_grad_many(int64_t n, const double *g5, double *dz)
 /* The roughness slot codes the material: >= 0 GGX, in (-1.5, 0) Lambertian */
 /* (-1 by convention), <= -1.5 transparent (-2 by convention).              */
 /* All directions are in the local frame (normal = +z).                     */
+/* Pinned by: the Lambertian pdf normalised and consistent with its         */
+/* sampler; the GGX distribution normalised, its sampler against its pdf,   */
+/* reciprocity and the energy bound (tests/test_oracle_pins.py); the        */
+/* dielectric Fresnel against the sine/tangent form, Snell's law, Schlick's */
+/* limits and the Fresnel-weighted lobe against its sampler                 */
+/* (tests/test_oracle_materials.py).                                        */
 /* ------------------------------------------------------------------------ */
 static int is_transparent(double rough) { return rough <= -1.5; }
 static int is_lambert(double rough) { return rough < 0.0 && rough > -1.5; }
@@ -468,6 +474,9 @@ int or_brdf_sample(double rough, const double wo[3], double x1, double x2, doubl
 /*   vMF(w; d, k) = k / (2 pi (1 - exp(-2k))) exp(k (d.w - 1)),             */
 /* optionally times a smooth occlusion mask of the world position and the   */
 /* direction, plus a constant.                                              */
+/* Pinned by: each normalised lobe integrating to 1 over the sphere         */
+/* (tests/test_oracle_pins.py); the coloured field training exactly as the  */
+/* monochrome field of its luminances (tests/test_oracle_colour.py).        */
 /* ------------------------------------------------------------------------ */
 /* The coloured field's channels (a monochrome field gives its value in all three). */
 void or_radiance_rgb(const or_field *f, const double x[3], const double w[3], double out[3])
@@ -594,6 +603,10 @@ void or_init_gamma(const or_config *cfg, double pi, int64_t n, double *gam)
 /* all evaluated in binary32 in this order. Frame change when the normals   */
 /* differ: the guide's mean direction is carried through the world into the */
 /* new frame (clamped to the horizon), the covariance is kept.              */
+/* Pinned by: identity motion copying Gamma exactly, an integer pan         */
+/* shifting it with exactly the newly exposed columns rejected, the depth,  */
+/* normal and off-screen rejections, and the frame change keeping the       */
+/* mean's world direction (tests/test_oracle_pins.py).                      */
 /* ------------------------------------------------------------------------ */
 static void frame_change(const double np_[3], const double nc[3], double *gm)
 {
@@ -689,6 +702,11 @@ void or_reproject(const or_config *cfg, const float *g0, const float *g1, const 
 /* independent of word 0, so still uniform given the choice); a guide draw  */
 /* that left the square takes its BRDF draw from word 3 and from the low    */
 /* bytes of words 0-2, bits the decision has not looked at.                 */
+/* Pinned by: the mixture pdf integrating to 1 (Lambert) and to the valid   */
+/* BRDF mass (GGX), the MIS weights at the samples, unbiased estimates of   */
+/* closed-form integrals (constant radiance, a lobe on the normal, GGX      */
+/* albedo) and BRDF-only draws on re-initialised pixels                     */
+/* (tests/test_oracle_pins.py).                                             */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double g5[5], chol[3], Z, pi_eff;
@@ -912,6 +930,11 @@ void or_sample(const or_config *cfg, const or_camera *cam, const or_field *fld, 
 /*   E <- ((1 - eta) pi M0 E + eta S) / A  for the five moments              */
 /*   pi <- clamp(A / B, 0.05, 0.95), k <- min(k + 1, kMax), W <- B.         */
 /* A frame without BRDF-strategy energy (b = 0) leaves Gamma unchanged.     */
+/* Pinned by: the population fixed point, a convex move toward the sample,  */
+/* continuity and luminance weighting, scale invariance, guide and wasted   */
+/* samples not training, and recovery of a known mixture from its samples   */
+/* (tests/test_oracle_pins.py); reuse weighting and the pick law            */
+/* (tests/test_oracle_reuse.py).                                            */
 /* ------------------------------------------------------------------------ */
 static void em_step(const or_config *cfg, double *gm, double a, double b, double s1x, double s1y,
                     double s2xx, double s2yy, double s2xy);
@@ -1130,7 +1153,8 @@ static void update_pixel_reuse(const or_config *cfg, const or_camera *cam, uint3
  * training. Writes each pixel's new Gamma (gam_out[8k..]), its estimate
  * (img[k * planes + c], planes = 3 for a coloured field, else 1) and the
  * smallest decision margin of its draws. For parity checks of full-size
- * frames on a sample of their pixels. */
+ * frames on a sample of their pixels. Pinned by equality, exact, with
+ * or_frame on the same pixels (tests/test_oracle_pixels.py). */
 void or_frame_pixels(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,
                      const float *g0, const float *g1, const float *g0p, const double *gam_prev_row,
                      int64_t n, const int32_t *xs, const int32_t *ys, double *gam_out, double *img,
@@ -1165,7 +1189,9 @@ void or_frame_pixels(const or_config *cfg, const or_camera *cam, const or_field 
 
 /* One whole frame: reprojection, sampling and training, pixel by pixel.
  * gam_prev and gam_out are HW x 8; samples S may have NULL planes except the
- * ones the training step reads (wx, wy, wz, radiance, strategy). */
+ * ones the training step reads (wx, wy, wz, radiance, strategy). A
+ * composition of the steps above, each pinned where it is defined; the reuse,
+ * material and colour forms of the frame are pinned in their own tests. */
 void or_frame(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,
               const float *g0, const float *g1, const float *g0p, const double *gam_prev,
               double *gam_out, uint8_t *accept, or_samples *S, double *img)
@@ -1209,7 +1235,9 @@ void or_frame(const or_config *cfg, const or_camera *cam, const or_field *fld, u
 
 /* Evaluate the mixture at caller-given world directions: for each pixel and
  * each of n directions, the pieces p_g, p_b, p_mix, the two balance weights,
- * f_r cos and the radiance. Output layout [k][n*HW + i] for k = 0..6. */
+ * f_r cos and the radiance. Output layout [k][n*HW + i] for k = 0..6.
+ * Pinned by the mixture-pdf integrals and the MIS weights at the samples,
+ * which read it (tests/test_oracle_pins.py). */
 void or_eval(const or_config *cfg, const or_camera *cam, const or_field *fld, const float *g0,
              const float *g1, const double *gam, const uint8_t *reinit, int n,
              const double *dirs /* [n*HW][3] */, double *out)
@@ -1241,7 +1269,7 @@ void or_eval(const or_config *cfg, const or_camera *cam, const or_field *fld, co
 }
 
 /* Per-pixel derived guide: mu, Sigma (regularised), Z, pi_eff. out [HW][8]:
- * mx, my, sxx, syy, sxy, Z, pi_eff, 0. */
+ * mx, my, sxx, syy, sxy, Z, pi_eff, 0. Z as pinned in or_rect_mass. */
 void or_derive_pixels(const or_config *cfg, const or_camera *cam, const float *g0,
                       const float *g1, const double *gam, const uint8_t *reinit, double *out)
 {
@@ -1354,6 +1382,8 @@ void or_second_moment(const or_config *cfg, const or_camera *cam, const or_field
 /* clamped, pi clamped), written back to Gamma as moments; k and W are kept.*/
 /* gam [HW][8] in/out, grad, m, v [HW][6] (m, v in/out). c1 = 1/(1-b1^t),   */
 /* c2 = 1/(1-b2^t) are the bias corrections of step t.                     */
+/* Pinned by Adam's first step in closed form and the projection onto     */
+/* the guide's domain (tests/test_oracle_pins.py).                         */
 /* ------------------------------------------------------------------------ */
 void or_adam(const or_config *cfg, int64_t n, double *gam, const double *grad, double *m, double *v,
              double lr, double b1, double b2, double eps, double c1, double c2)
