@@ -686,6 +686,8 @@ def run_gpu(args, ws, rank, local):
     # neighbour-VPL reuse (two passes per frame), FP16 Gamma, window radius REUSE_R
     forms["reuse"] = run_form(par, sc, fld, g0d, g1d, "f16", args.warmup, args.steps, flush, keep, rank,
                               reuse_radius=REUSE_R)
+    # the precision form's other storage type, timed and scored like FP16
+    forms["bf16"] = run_form(par, sc, fld, g0d, g1d, "bf16", args.warmup, args.steps, flush, keep, rank)
     staged_ms = run_staged(par, sc, fld, g0d, g1d, "f16", args.warmup, args.steps, flush)
     # the same frames with the field's lobes coloured (three image planes)
     rgb_ms = run_form(par, sc, scenes.coloured(fld, 2), g0d, g1d, "f16", args.warmup, args.steps, flush, set(),
@@ -702,7 +704,7 @@ def run_gpu(args, ws, rank, local):
     if keep:
         ref = reference_images(par, sc, fld, g0d, g1d, sorted(keep))
         m = {}
-        for dt in ("f32", "f16", "reuse"):
+        for dt in ("f32", "f16", "bf16", "reuse"):
             acc = 0.0
             for t in sorted(keep):
                 d = (forms[dt][1][t].double() - ref[t].double())
@@ -710,7 +712,8 @@ def run_gpu(args, ws, rank, local):
             m[dt] = acc / len(keep)
         mse = {"frames": [min(keep), max(keep)], "reference": "%d spp" % REF_SPP, "fp32": m["f32"],
                "fp16": m["f16"], "ratio_fp16_over_fp32": m["f16"] / m["f32"],
-               "matched": bool(m["f16"] <= 1.02 * m["f32"]), "fp16_reuse": m["reuse"]}
+               "matched": bool(m["f16"] <= 1.02 * m["f32"]), "fp16_reuse": m["reuse"], "bf16": m["bf16"],
+               "ratio_bf16_over_fp32": m["bf16"] / m["f32"]}
 
     e2e_ms, h2d, d2h = run_e2e(par, sc, fld, g0h, g1h, "f16", args.warmup, args.steps, rank)
     del g0h, g1h, g0d, g1d
@@ -725,7 +728,7 @@ def run_gpu(args, ws, rank, local):
     rounding = None if args.no_temporal else run_rounding()
 
     res = {}
-    for dt in ("f32", "f16", "reuse"):
+    for dt in ("f32", "f16", "bf16", "reuse"):
         ms = forms[dt][0]
         rate, tot = job_rate(ws, sum(ms) / 1e3, hw * len(ms))
         res[dt] = {"mpix_s": rate / 1e6, "ms_per_step": 1e3 * tot / len(ms),
@@ -760,6 +763,8 @@ def run_gpu(args, ws, rank, local):
                    "parallelism": "dp%d (independent 1080p streams per GPU)" % ws},
         "fp32_plain": {"value": res["f32"]["mpix_s"], "ms_per_step": res["f32"]["ms_per_step"],
                        "roofline_frac": res["f32"]["gbs"] / peak},
+        "bf16": {"value": res["bf16"]["mpix_s"], "ms_per_step": res["bf16"]["ms_per_step"],
+                 "roofline_frac": res["bf16"]["gbs"] / peak},
         "mse": mse,
         "rgb": {"ms_per_step": sum(rgb_ms) / len(rgb_ms), "gamma_storage": "f16",
                 "mpix_s": hw * len(rgb_ms) / sum(rgb_ms) / 1e3, "algorithmic_bytes_per_pixel": 64 + 16 + 12,
