@@ -36,6 +36,7 @@ REUSE_R = 2
 # Gamma(t-1), the G-buffer and the VPL (84 B; neighbours' VPLs come from
 # cache) and writes Gamma(t) (16 B)
 BYTES_PER_PIXEL["reuse"] = (64 + 4 + 20) + (64 + 20 + 16)
+BYTES_PER_PIXEL["spp3"] = BYTES_PER_PIXEL["f16"]      # samples never touch memory in the fused pass
 REF_SPP = 256
 # one projected Adam step on FP16 Gamma: Gamma read + write (32 B), the
 # gradient (24 B), m and v each read and written (4 x 24 B in binary32,
@@ -688,6 +689,9 @@ def run_gpu(args, ws, rank, local):
                               reuse_radius=REUSE_R)
     # the precision form's other storage type, timed and scored like FP16
     forms["bf16"] = run_form(par, sc, fld, g0d, g1d, "bf16", args.warmup, args.steps, flush, keep, rank)
+    # three samples per pixel without reuse, for comparing the two ways to
+    # spend guide-pass time (here a sample's radiance is analytic and cheap)
+    forms["spp3"] = run_form(par, sc, fld, g0d, g1d, "f16", args.warmup, args.steps, flush, keep, rank, spp=3)
     staged_ms = run_staged(par, sc, fld, g0d, g1d, "f16", args.warmup, args.steps, flush)
     # the same frames with the field's lobes coloured (three image planes)
     rgb_ms = run_form(par, sc, scenes.coloured(fld, 2), g0d, g1d, "f16", args.warmup, args.steps, flush, set(),
@@ -704,7 +708,7 @@ def run_gpu(args, ws, rank, local):
     if keep:
         ref = reference_images(par, sc, fld, g0d, g1d, sorted(keep))
         m = {}
-        for dt in ("f32", "f16", "bf16", "reuse"):
+        for dt in ("f32", "f16", "bf16", "reuse", "spp3"):
             acc = 0.0
             for t in sorted(keep):
                 d = (forms[dt][1][t].double() - ref[t].double())
@@ -713,7 +717,7 @@ def run_gpu(args, ws, rank, local):
         mse = {"frames": [min(keep), max(keep)], "reference": "%d spp" % REF_SPP, "fp32": m["f32"],
                "fp16": m["f16"], "ratio_fp16_over_fp32": m["f16"] / m["f32"],
                "matched": bool(m["f16"] <= 1.02 * m["f32"]), "fp16_reuse": m["reuse"], "bf16": m["bf16"],
-               "ratio_bf16_over_fp32": m["bf16"] / m["f32"]}
+               "ratio_bf16_over_fp32": m["bf16"] / m["f32"], "fp16_3spp": m["spp3"]}
 
     e2e_ms, h2d, d2h = run_e2e(par, sc, fld, g0h, g1h, "f16", args.warmup, args.steps, rank)
     del g0h, g1h, g0d, g1d
@@ -728,7 +732,7 @@ def run_gpu(args, ws, rank, local):
     rounding = None if args.no_temporal else run_rounding()
 
     res = {}
-    for dt in ("f32", "f16", "bf16", "reuse"):
+    for dt in ("f32", "f16", "bf16", "reuse", "spp3"):
         ms = forms[dt][0]
         rate, tot = job_rate(ws, sum(ms) / 1e3, hw * len(ms))
         res[dt] = {"mpix_s": rate / 1e6, "ms_per_step": 1e3 * tot / len(ms),
@@ -778,6 +782,9 @@ def run_gpu(args, ws, rank, local):
         "reuse": {"radius": REUSE_R, "gamma_storage": "f16", "kernels_per_frame": 2,
                   "value": res["reuse"]["mpix_s"], "ms_per_step": res["reuse"]["ms_per_step"],
                   "hbm_frac": res["reuse"]["gbs"] / peak,
+                  "plain_3spp": {"ms_per_step": res["spp3"]["ms_per_step"],
+                                            "image_mse": mse["fp16_3spp"] if mse else None,
+                                            "reuse_image_mse": mse["fp16_reuse"] if mse else None},
                   "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL["reuse"]},
         "roofline": {"bound": "hbm", "achieved": main["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": main["gbs"] / peak, "peak_kind": peak_kind,
