@@ -100,8 +100,11 @@ def _load():
                 "or_adam": [_P, C.c_int64, _P, _P, _P, _P, C.c_double, C.c_double, C.c_double,
                             C.c_double, C.c_double, C.c_double],
                 "or_reuse_picks": [_P, C.c_double, C.c_uint32, C.c_uint32, _P, _P, _P],
-                "or_frame_pixels": [_P, _P, _P, C.c_uint32, _P, _P, _P, _P, C.c_int64, _P, _P, _P, _P, _P],
+                "or_frame_pixels": [_P, _P, _P, C.c_uint32, _P, _P, _P, _P, C.c_int64, C.c_int64, _P, _P, _P,
+                                    _P, _P, _P],
                 "or_brdf_cos_f0": [C.c_double, C.c_double, C.c_double, _P, _P],
+                "or_camera_ray": [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P],
+                "or_ground_truth": [_P, _P, _P, _P, _P, C.c_int64, _P, _P, C.c_double, _P, _P],
                 "or_dielectric_fresnel": [C.c_double],
                 "or_set_threads": [C.c_int],
                 "or_max_threads": [],
@@ -375,22 +378,30 @@ def reuse_picks(cfg, k, pix, frame_idx):
     return dx[:n].copy(), dy[:n].copy(), sm[:n].copy()
 
 
-def frame_pixels(cfg, cam, field, frame_idx, g0, g1, g0_prev, gam_prev_row, xs, ys):
-    """Chosen pixels of one frame, each computed alone, from a previous Gamma
-    that is gam_prev_row for every pixel. Returns (gamma [n, 8], img [n] or
-    [n, 3] for a coloured field, margin [n])."""
+def frame_pixels(cfg, cam, field, frame_idx, g0, g1, g0_prev, gam_prev, xs, ys, with_accept=False):
+    """Chosen pixels of one frame, each computed alone. gam_prev is either the
+    whole previous Gamma [H*W, 8] (gathered at each pixel's reprojected
+    pixel) or one row [8] shared by every pixel. Returns (gamma [n, 8], img
+    [n] or [n, 3] for a coloured field, margin [n]) and, with with_accept,
+    the accept flags [n] as a fourth element."""
     hw = cfg.width * cfg.height
     g0, g1, g0p = _f32(g0, (hw, 4)), _f32(g1, (hw, 4)), _f32(g0_prev, (hw, 4))
-    row = _f64(gam_prev_row, (8,))
+    gp = _f64(gam_prev)
+    if gp.size == 8:
+        gp, stride = gp.reshape(8), 0
+    else:
+        gp, stride = gp.reshape(hw, 8), 8
     xs = np.ascontiguousarray(xs, np.int32)
     ys = np.ascontiguousarray(ys, np.int32)
     n = len(xs)
     planes = 3 if field.rgb else 1
     out, img, margin = np.empty((n, 8)), np.empty(n * planes), np.empty(n)
+    acc = np.empty(n, np.uint8)
     _load().or_frame_pixels(C.byref(cfg), C.byref(cam), C.byref(field), int(frame_idx) & 0xFFFFFFFF,
-                            _ptr(g0), _ptr(g1), _ptr(g0p), _ptr(row), int(n), _ptr(xs), _ptr(ys),
-                            _ptr(out), _ptr(img), _ptr(margin))
-    return out, (img if planes == 1 else img.reshape(n, 3)), margin
+                            _ptr(g0), _ptr(g1), _ptr(g0p), _ptr(gp), stride, int(n), _ptr(xs), _ptr(ys),
+                            _ptr(out), _ptr(img), _ptr(margin), _ptr(acc))
+    res = (out, (img if planes == 1 else img.reshape(n, 3)), margin)
+    return res + (acc,) if with_accept else res
 
 
 def frame(cfg, cam, field, frame_idx, g0, g1, g0_prev, gam_prev):
@@ -407,6 +418,30 @@ def frame(cfg, cam, field, frame_idx, g0, g1, g0_prev, gam_prev):
                      _ptr(g0), _ptr(g1), _ptr(g0p), _ptr(gp), _ptr(out), _ptr(acc), C.byref(s),
                      _ptr(img))
     return out, acc, arrs, img
+
+
+def camera_ray(cam, width, height, x, y):
+    """Primary ray of pixel (x, y): (origin [3], unit direction [3])."""
+    o, d = np.empty(3), np.empty(3)
+    _load().or_camera_ray(C.byref(cam), int(width), int(height), int(x), int(y), _ptr(o), _ptr(d))
+    return o, d
+
+
+def ground_truth(cfg, cam, field, g0, g1, xs, ys, tol_rel=1e-8, with_error=False):
+    """FP64 ground truth I(p) = int L f_r cos dw of chosen pixels: [n] (or
+    [n, 3] for a coloured field); with with_error also the cubature's error
+    bound [n]."""
+    hw = cfg.width * cfg.height
+    g0, g1 = _f32(g0, (hw, 4)), _f32(g1, (hw, 4))
+    xs = np.ascontiguousarray(xs, np.int32)
+    ys = np.ascontiguousarray(ys, np.int32)
+    n = len(xs)
+    planes = 3 if field.rgb else 1
+    out, err = np.empty(n * planes), np.empty(n)
+    _load().or_ground_truth(C.byref(cfg), C.byref(cam), C.byref(field), _ptr(g0), _ptr(g1), int(n), _ptr(xs),
+                            _ptr(ys), float(tol_rel), _ptr(out), _ptr(err))
+    out = out if planes == 1 else out.reshape(n, 3)
+    return (out, err) if with_error else out
 
 
 EVAL_KEYS = ("pg", "pb", "pmix", "w_guide", "w_brdf", "fcos", "radiance")

@@ -522,8 +522,17 @@ double or_radiance(const or_field *f, const double x[3], const double w[3])
 /* ------------------------------------------------------------------------ */
 /* Camera: primary ray of pixel (x, y); the view direction w_o is the       */
 /* reversed ray and the shading point is origin + depth * dir.              */
+/* Orthographic: from origin + (x+0.5) s right + (y+0.5) s up along fwd      */
+/* (s the pixel size). Pinhole: from origin along fwd + sx right + sy up,   */
+/* normalised, sx = (2 (x+0.5)/W - 1) tan(fov_v/2) W/H, sy = (1 - 2 (y+0.5)/H)*/
+/* tan(fov_v/2): row 0 at the top, the image's horizontal half-angle at     */
+/* atan(tan(fov_v/2) W/H).                                                  */
+/* Pinned by: shading points landing on the synthetic scenes' surfaces (the */
+/* panned heightfield, the orbit's ground and quads), the centre pixel's    */
+/* ray along fwd and the horizontal field of view at the screen's edge      */
+/* (tests/test_oracle_ground_truth.py).                                     */
 /* ------------------------------------------------------------------------ */
-static void camera_ray(const or_camera *c, int W, int H, int x, int y, double o[3], double d[3])
+void or_camera_ray(const or_camera *c, int W, int H, int x, int y, double o[3], double d[3])
 {
     if (c->kind == 0) {
         double sx = (x + 0.5) * c->pixel_size, sy = (y + 0.5) * c->pixel_size;
@@ -721,14 +730,15 @@ static void cholesky(const double g5[5], double c[3])
     c[2] = sqrt(g5[3] - c[1] * c[1]);
 }
 
-static void pixel_setup(const or_config *cfg, const or_camera *cam, int x, int y,
-                        const float *g0, const float *g1, const double *gm, int reinit,
-                        pixel_ctx *p)
+/* The surface of pixel (x, y): normal, shading point, local view direction
+ * and material. */
+static void surface_setup(const or_config *cfg, const or_camera *cam, int x, int y,
+                          const float *g0, const float *g1, pixel_ctx *p)
 {
     int W = cfg->width, H = cfg->height;
     int64_t i = (int64_t)y * W + x;
     double o[3], d[3];
-    camera_ray(cam, W, H, x, y, o, d);
+    or_camera_ray(cam, W, H, x, y, o, d);
     double depth = g0[4 * i + 3];
     double wo[3] = {-d[0], -d[1], -d[2]};
     for (int k = 0; k < 3; ++k) { p->n[k] = g0[4 * i + k]; p->pos[k] = o[k] + depth * d[k]; }
@@ -737,6 +747,13 @@ static void pixel_setup(const or_config *cfg, const or_camera *cam, int x, int y
     if (!cfg->transparent && is_transparent(p->rough)) p->rough = -1.0;   /* the code is Lambertian then */
     p->albedo = g1[4 * i + 3];
     p->f0 = cfg->ggx_f0;
+}
+
+static void pixel_setup(const or_config *cfg, const or_camera *cam, int x, int y,
+                        const float *g0, const float *g1, const double *gm, int reinit,
+                        pixel_ctx *p)
+{
+    surface_setup(cfg, cam, x, y, g0, g1, p);
     derive_gauss(cfg, gm, p->g5);
     cholesky(p->g5, p->chol);
     p->Z = or_rect_mass(p->g5);
@@ -1148,17 +1165,21 @@ static void update_pixel_reuse(const or_config *cfg, const or_camera *cam, uint3
 }
 
 /* Chosen pixels (xs[k], ys[k]) of one frame, each computed alone (no
- * neighbour reuse): reprojection against a previous Gamma that is the same
- * row gam_prev_row for every pixel (a screen's first frame), sampling and
- * training. Writes each pixel's new Gamma (gam_out[8k..]), its estimate
- * (img[k * planes + c], planes = 3 for a coloured field, else 1) and the
- * smallest decision margin of its draws. For parity checks of full-size
- * frames on a sample of their pixels. Pinned by equality, exact, with
- * or_frame on the same pixels (tests/test_oracle_pixels.py). */
+ * neighbour reuse): reprojection against the previous Gamma, sampling and
+ * training. The previous Gamma is either a whole frame (gstride = 8: row q
+ * at gam_prev + 8 q, gathered at the reprojected pixel q, e.g. the state
+ * another implementation reached) or one row shared by every pixel
+ * (gstride = 0: a screen's first frame). Writes each pixel's new Gamma
+ * (gam_out[8k..]), its estimate (img[k * planes + c], planes = 3 for a
+ * coloured field, else 1), the smallest decision margin of its draws and,
+ * when accept is not NULL, whether its history was reused. For parity
+ * checks of full-size frames on a sample of their pixels. Pinned by
+ * equality, exact, with or_frame on the same pixels
+ * (tests/test_oracle_pixels.py). */
 void or_frame_pixels(const or_config *cfg, const or_camera *cam, const or_field *fld, uint32_t frame,
-                     const float *g0, const float *g1, const float *g0p, const double *gam_prev_row,
-                     int64_t n, const int32_t *xs, const int32_t *ys, double *gam_out, double *img,
-                     double *margin)
+                     const float *g0, const float *g1, const float *g0p, const double *gam_prev,
+                     int64_t gstride, int64_t n, const int32_t *xs, const int32_t *ys, double *gam_out,
+                     double *img, double *margin, uint8_t *accept)
 {
     int spp = cfg->spp, planes = fld->rgb ? 3 : 1;
 #pragma omp parallel
@@ -1174,7 +1195,8 @@ void or_frame_pixels(const or_config *cfg, const or_camera *cam, const or_field 
             int x = xs[k], y = ys[k];
             int32_t q;
             double *gm = gam_out + 8 * k, im[3];
-            int acc = reproject_pixel_s(cfg, x, y, g0, g1, g0p, gam_prev_row, 0, gm, &q);
+            int acc = reproject_pixel_s(cfg, x, y, g0, g1, g0p, gam_prev, gstride, gm, &q);
+            if (accept) accept[k] = (uint8_t)acc;
             sample_pixel_s(cfg, cam, fld, frame, x, y, g0, g1, gm, !acc, &S, im, 0, 1);
             update_pixel_s(cfg, cam, x, y, g0, g1, gm, !acc, S.wx, S.wy, S.wz, S.radiance, S.strategy, 0, 1);
             double m = 1.0;
@@ -1409,6 +1431,342 @@ void or_adam(const or_config *cfg, int64_t n, double *gam, const double *grad, d
         double k = gm[G_K], wmass = gm[G_W];
         theta_to_gamma(th, gm);
         gm[G_K] = k; gm[G_W] = wmass;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ground truth of a pixel (Eq. 1): the reflected radiance                  */
+/*   I(p) = int_H L_i(x, w) f_r(w_o, w) cos(theta) dw,                      */
+/* the value whose estimate F the pass returns. FP64 adaptive cubature in   */
+/* the polar coordinates of the disk that M lifts to the hemisphere:        */
+/*   w_local = (r cos phi sqrt(2 - r^2), r sin phi sqrt(2 - r^2), 1 - r^2),  */
+/*   dw = 2 r dr dphi  (the equal-area lift doubles areas),                 */
+/* r in [0, 1], phi in [0, 2 pi): the horizon is the edge r = 1, so the     */
+/* integrand is smooth inside the domain. Each cell carries a tensor        */
+/* Gauss-Legendre rule of GT_NG x GT_NG nodes and an error: how far its     */
+/* rule is from the sum over its halves along r, or along phi, whichever is */
+/* further. Globally adaptive: the cell with the largest error is halved    */
+/* until the summed error is within tol_rel of the result; before that,     */
+/* whatever the error, every cell that is large against its distance to a   */
+/* known peak of the integrand is halved: each vMF lobe (width 1/sqrt(kappa);*/
+/* a lobe below the horizon at its horizon point) and the GGX mirror        */
+/* direction (width 2 alpha), so that no peak can hide between nodes.      */
+/* A transparent surface sends the view along two deltas:                   */
+/*   I = albedo (F L(w_r) + (1 - F) L(w_t)),  F the Fresnel reflectance.     */
+/* A coloured field has one integral per channel.                           */
+/* Pinned by: constant radiance (I = albedo c), a lobe on the normal and a  */
+/* lobe away from the horizon in closed form, the GGX directional albedo by */
+/* an independent quadrature over half vectors, a masked field against a    */
+/* brute-force grid on the square, and the mean of the pass's own estimator */
+/* on workload pixels (tests/test_oracle_ground_truth.py).                  */
+/* ------------------------------------------------------------------------ */
+#define GT_NG 6
+/* integrand evaluations per pixel after which cells are accepted as they are
+ * (their differences still enter the reported error): a tolerance below the
+ * integrand's own rounding, e.g. 1e-10 at a GGX peak of alpha = 1e-4, where
+ * D loses ~1e-8 of its relative precision, would refine without end */
+#define GT_MAX_EVALS 4000000L
+#define GT_MAX_PEAKS 9
+
+typedef struct {
+    const or_field *fld;
+    pixel_ctx p;                        /* surface only: normal, position, view, material */
+    double t[3], b[3];                  /* basis around the normal */
+    int planes;
+    int n_peaks;
+    double peak[GT_MAX_PEAKS][3], width[GT_MAX_PEAKS];
+    double gx[GT_NG], gw[GT_NG];        /* Gauss-Legendre nodes and weights on [-1, 1] */
+    double tol_rel;                     /* relative tolerance of the whole integral */
+    long evals;                         /* integrand evaluations so far */
+} gt_ctx;
+
+/* Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on the
+ * Legendre polynomial P_n from the usual cosine starting points, with P_n and
+ * its derivative from the three-term recurrence. */
+static void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static void gt_dir(double r, double phi, double wl[3])
+{
+    double s = sqrt(2.0 - r * r);
+    wl[0] = r * cos(phi) * s; wl[1] = r * sin(phi) * s; wl[2] = 1.0 - r * r;
+}
+
+/* Integrand times the Jacobian 2 r at (r, phi). */
+static void gt_eval(const gt_ctx *c, double r, double phi, double out[3])
+{
+    double wl[3], ww[3];
+    gt_dir(r, phi, wl);
+    double fc = or_brdf_cos_f0(c->p.rough, c->p.albedo, c->p.f0, c->p.wo_l, wl);
+    out[0] = out[1] = out[2] = 0.0;
+    if (fc == 0.0) return;
+    for (int i = 0; i < 3; ++i) ww[i] = wl[0] * c->t[i] + wl[1] * c->b[i] + wl[2] * c->p.n[i];
+    if (c->planes == 3) {
+        double L[3];
+        or_radiance_rgb(c->fld, c->p.pos, ww, L);
+        for (int k = 0; k < 3; ++k) out[k] = L[k] * fc * 2.0 * r;
+    } else {
+        out[0] = or_radiance(c->fld, c->p.pos, ww) * fc * 2.0 * r;
+    }
+}
+
+/* The tensor rule on [r0, r1] x [p0, p1]. */
+static void gt_rule(gt_ctx *c, double r0, double r1, double p0, double p1, double q[3])
+{
+    c->evals += GT_NG * GT_NG;
+    double hr = 0.5 * (r1 - r0), hp = 0.5 * (p1 - p0), mr = 0.5 * (r0 + r1), mp = 0.5 * (p0 + p1);
+    q[0] = q[1] = q[2] = 0.0;
+    for (int i = 0; i < GT_NG; ++i)
+        for (int j = 0; j < GT_NG; ++j) {
+            double v[3];
+            gt_eval(c, mr + hr * c->gx[i], mp + hp * c->gx[j], v);
+            for (int k = 0; k < 3; ++k) q[k] += c->gw[i] * c->gw[j] * v[k];
+        }
+    for (int k = 0; k < 3; ++k) q[k] *= hr * hp;
+}
+
+/* Whether a cell is large against its distance to a peak: its radius (the
+ * largest chord from its centre to a corner or an edge midpoint) above a
+ * quarter of max(distance, width). */
+static int gt_must_split(const gt_ctx *c, double r0, double r1, double p0, double p1)
+{
+    double ctr[3], pts[8][3];
+    gt_dir(0.5 * (r0 + r1), 0.5 * (p0 + p1), ctr);
+    double rs[3] = {r0, 0.5 * (r0 + r1), r1}, ps[3] = {p0, 0.5 * (p0 + p1), p1};
+    int m = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            if (a != 1 || b != 1) gt_dir(rs[a], ps[b], pts[m++]);
+    double rad = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        double dx = pts[k][0] - ctr[0], dy = pts[k][1] - ctr[1], dz = pts[k][2] - ctr[2];
+        double d = sqrt(dx * dx + dy * dy + dz * dz);
+        if (d > rad) rad = d;
+    }
+    for (int j = 0; j < c->n_peaks; ++j) {
+        double dx = c->peak[j][0] - ctr[0], dy = c->peak[j][1] - ctr[1], dz = c->peak[j][2] - ctr[2];
+        double dist = sqrt(dx * dx + dy * dy + dz * dz) - rad;
+        if (dist < 0.0) dist = 0.0;
+        double scale = dist > c->width[j] ? dist : c->width[j];
+        if (rad > 0.25 * scale) return 1;
+    }
+    return 0;
+}
+
+/* One cell of the adaptive cubature: its bounds, its rule's halves along r
+ * (ra, rb) and along phi (pa, pb), its estimate (the halves' sum along its
+ * worse axis), that axis, its error (the larger difference between its rule
+ * and the sum of its halves along either axis, so an error along either axis
+ * shows) and whether a peak forces its split. */
+typedef struct {
+    double r0, r1, p0, p1;
+    double ra[3], rb[3], pa[3], pb[3];
+    double est[3], err;
+    int along_r, forced;
+} gt_cellrec;
+
+static void gt_make_cell(gt_ctx *c, double r0, double r1, double p0, double p1, const double q[3], gt_cellrec *e)
+{
+    double rm = 0.5 * (r0 + r1), pm = 0.5 * (p0 + p1), dr = 0.0, dp = 0.0;
+    e->r0 = r0; e->r1 = r1; e->p0 = p0; e->p1 = p1;
+    gt_rule(c, r0, rm, p0, p1, e->ra);
+    gt_rule(c, rm, r1, p0, p1, e->rb);
+    gt_rule(c, r0, r1, p0, pm, e->pa);
+    gt_rule(c, r0, r1, pm, p1, e->pb);
+    double sr[3], sp[3];
+    for (int k = 0; k < 3; ++k) {
+        sr[k] = e->ra[k] + e->rb[k];
+        sp[k] = e->pa[k] + e->pb[k];
+        if (fabs(sr[k] - q[k]) > dr) dr = fabs(sr[k] - q[k]);
+        if (fabs(sp[k] - q[k]) > dp) dp = fabs(sp[k] - q[k]);
+    }
+    for (int k = 0; k < 3; ++k) e->est[k] = dr >= dp ? sr[k] : sp[k];
+    e->err = dr > dp ? dr : dp;
+    e->forced = gt_must_split(c, r0, r1, p0, p1);
+    /* a forced split cuts the longer side (radial extent ~ sqrt(2) dr,
+     * azimuthal ~ sqrt(2) r1 dphi: a cell at the pole is cut in r, not into
+     * ever thinner wedges); any other split cuts the worse axis */
+    e->along_r = e->forced ? (r1 - r0) >= r1 * (p1 - p0) : dr >= dp;
+}
+
+/* max-heap of cells: forced splits first, then by error */
+static int gt_before(const gt_cellrec *a, const gt_cellrec *b)
+{
+    if (a->forced != b->forced) return a->forced > b->forced;
+    return a->err > b->err;
+}
+
+static void gt_push(gt_cellrec *h, long *n, const gt_cellrec *e)
+{
+    long i = (*n)++;
+    h[i] = *e;
+    while (i > 0) {
+        long up = (i - 1) / 2;
+        if (!gt_before(&h[i], &h[up])) break;
+        gt_cellrec t = h[i]; h[i] = h[up]; h[up] = t;
+        i = up;
+    }
+}
+
+static void gt_pop(gt_cellrec *h, long *n, gt_cellrec *out)
+{
+    *out = h[0];
+    h[0] = h[--(*n)];
+    long i = 0;
+    for (;;) {
+        long l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *n && gt_before(&h[l], &h[m])) m = l;
+        if (r < *n && gt_before(&h[r], &h[m])) m = r;
+        if (m == i) break;
+        gt_cellrec t = h[i]; h[i] = h[m]; h[m] = t;
+        i = m;
+    }
+}
+
+/* Global adaptive cubature over the disk from a base grid of 4 x 16 cells:
+ * the cell first in the heap is split while a peak forces a split or the
+ * summed error exceeds tol_rel times the summed estimate, within
+ * GT_MAX_EVALS evaluations. The sums are kept as the cells change and
+ * summed afresh every 1024 splits and at the end. */
+static void gt_sums(const gt_cellrec *h, long n, double tot[3], double *terr)
+{
+    tot[0] = tot[1] = tot[2] = 0.0;
+    *terr = 0.0;
+    for (long i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) tot[k] += h[i].est[k];
+        *terr += h[i].err;
+    }
+}
+
+static void gt_integrate(gt_ctx *c, double out[3], double *err)
+{
+    long cap = GT_MAX_EVALS / (4 * GT_NG * GT_NG) + 256, n = 0;
+    gt_cellrec *h = malloc(sizeof(gt_cellrec) * (size_t)cap);
+    c->evals = 0;
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 16; ++b) {
+            double r0 = 0.25 * a, r1 = 0.25 * (a + 1), p0 = 2.0 * M_PI * b / 16.0, p1 = 2.0 * M_PI * (b + 1) / 16.0;
+            double q[3];
+            gt_cellrec e;
+            gt_rule(c, r0, r1, p0, p1, q);
+            gt_make_cell(c, r0, r1, p0, p1, q, &e);
+            gt_push(h, &n, &e);
+        }
+    double tot[3], terr;
+    gt_sums(h, n, tot, &terr);
+    for (long it = 1;; ++it) {
+        double mag = 0.0;
+        for (int k = 0; k < 3; ++k) mag = fabs(tot[k]) > mag ? fabs(tot[k]) : mag;
+        if (!(h[0].forced || terr > c->tol_rel * mag) || c->evals > GT_MAX_EVALS || n + 2 > cap) break;
+        gt_cellrec e, ca, cb;
+        gt_pop(h, &n, &e);
+        if (e.along_r) {
+            double rm = 0.5 * (e.r0 + e.r1);
+            gt_make_cell(c, e.r0, rm, e.p0, e.p1, e.ra, &ca);
+            gt_make_cell(c, rm, e.r1, e.p0, e.p1, e.rb, &cb);
+        } else {
+            double pm = 0.5 * (e.p0 + e.p1);
+            gt_make_cell(c, e.r0, e.r1, e.p0, pm, e.pa, &ca);
+            gt_make_cell(c, e.r0, e.r1, pm, e.p1, e.pb, &cb);
+        }
+        gt_push(h, &n, &ca);
+        gt_push(h, &n, &cb);
+        for (int k = 0; k < 3; ++k) tot[k] += ca.est[k] + cb.est[k] - e.est[k];
+        terr += ca.err + cb.err - e.err;
+        if (it % 1024 == 0) gt_sums(h, n, tot, &terr);
+    }
+    gt_sums(h, n, out, err);
+    free(h);
+}
+
+static void gt_add_peak(gt_ctx *c, const double l[3], double width)
+{
+    if (c->n_peaks >= GT_MAX_PEAKS) return;
+    double v[3] = {l[0], l[1], l[2]};
+    if (v[2] < 0.0) {   /* below the horizon: the integrand peaks at the nearest horizon point */
+        double h = sqrt(v[0] * v[0] + v[1] * v[1]);
+        if (h == 0.0) return;
+        v[0] /= h; v[1] /= h; v[2] = 0.0;
+    }
+    for (int k = 0; k < 3; ++k) c->peak[c->n_peaks][k] = v[k];
+    c->width[c->n_peaks] = width;
+    ++c->n_peaks;
+}
+
+/* Ground truth of pixels (xs[k], ys[k]): out[k * planes + c] (planes = 3 for
+ * a coloured field, else 1); err[k] (nullable) receives the sum of the
+ * accepted cells' differences, a bound on the error of the result. */
+void or_ground_truth(const or_config *cfg, const or_camera *cam, const or_field *fld, const float *g0,
+                     const float *g1, int64_t n, const int32_t *xs, const int32_t *ys, double tol_rel,
+                     double *out, double *err)
+{
+    double gx[GT_NG], gw[GT_NG];
+    gauss_legendre(GT_NG, gx, gw);
+    int planes = fld->rgb ? 3 : 1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < n; ++k) {
+        gt_ctx c;
+        memset(&c, 0, sizeof(c));
+        c.fld = fld;
+        c.planes = planes;
+        memcpy(c.gx, gx, sizeof(gx));
+        memcpy(c.gw, gw, sizeof(gw));
+        surface_setup(cfg, cam, xs[k], ys[k], g0, g1, &c.p);
+        or_basis(c.p.n, c.t, c.b);
+        double res[3] = {0.0, 0.0, 0.0}, e = 0.0;
+        if (is_transparent(c.p.rough)) {
+            /* the two deltas of the dielectric (Fresnel-weighted, tinted) */
+            double ci = c.p.wo_l[2];
+            if (ci > 0.0) {
+                double fr = or_dielectric_fresnel(ci), eta = 1.0 / DIELECTRIC_IOR;
+                double ct = sqrt(1.0 - eta * eta * (1.0 - ci * ci));
+                double lr[3] = {-c.p.wo_l[0], -c.p.wo_l[1], ci};
+                double lt[3] = {-eta * c.p.wo_l[0], -eta * c.p.wo_l[1], -ct};
+                double wr[3], wt[3], Lr[3], Lt[3];
+                to_world(c.p.n, lr, wr);
+                to_world(c.p.n, lt, wt);
+                if (planes == 3) {
+                    or_radiance_rgb(fld, c.p.pos, wr, Lr);
+                    or_radiance_rgb(fld, c.p.pos, wt, Lt);
+                } else {
+                    Lr[0] = or_radiance(fld, c.p.pos, wr);
+                    Lt[0] = or_radiance(fld, c.p.pos, wt);
+                }
+                for (int q = 0; q < planes; ++q) res[q] = c.p.albedo * (fr * Lr[q] + (1.0 - fr) * Lt[q]);
+            }
+        } else {
+            for (int j = 0; j < fld->n_lobes; ++j) {
+                double dl[3];
+                to_local(c.p.n, fld->dir[j], dl);
+                gt_add_peak(&c, dl, 1.0 / sqrt(fld->kappa[j]));
+            }
+            if (c.p.rough >= 0.0) {
+                double mir[3] = {-c.p.wo_l[0], -c.p.wo_l[1], c.p.wo_l[2]};
+                double w = 2.0 * ggx_alpha(c.p.rough);
+                gt_add_peak(&c, mir, w);
+            }
+            c.tol_rel = tol_rel;
+            gt_integrate(&c, res, &e);
+        }
+        for (int q = 0; q < planes; ++q) out[k * planes + q] = res[q];
+        if (err) err[k] = e;
     }
 }
 

@@ -333,8 +333,13 @@ def test_unbiased_constant_radiance_lambert():
     F, s = _unbiased_case(fld, _gam_block(256), albedo=0.8)
     m, se = F.mean(), F.std() / math.sqrt(F.size)
     assert abs(m - 0.8 * 1.7) < 4 * se + 1e-12
+    # each draw's estimate is L f_r cos / p_mix: with the normal +z and
+    # constant radiance, F p_mix = 1.7 (albedo / pi) w_z for every valid draw
     ok = s["pdf"] > 0
-    assert np.abs(s["mis"][ok] - 0).max() <= 1.0
+    assert ok.mean() > 0.99
+    lhs = s["estimate"][ok] * s["pdf"][ok]
+    rhs = 1.7 * float(np.float32(0.8)) / math.pi * s["wz"][ok]
+    assert np.allclose(lhs, rhs, rtol=1e-12, atol=0)
 
 
 def test_unbiased_vmf_lobe_on_normal_lambert():
