@@ -30,6 +30,8 @@ WORKLOAD = ("1920x1080, 1 spp, 60 frames: orthographic camera panning 2 px/frame
 BYTES_PER_PIXEL = {"f32": (32 + 16 + 16 + 16) + (32 + 4), "f16": (16 + 16 + 16 + 16) + (16 + 4),
                    "bf16": (16 + 16 + 16 + 16) + (16 + 4)}
 MSE_FRAMES = range(30, 60)
+MSE_RUN_FRAMES = 60            # the MSE leg runs its own 60-frame pass, whatever --steps is
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 REUSE_R = 2
 # with reuse the frame is two passes: path tracing reads Gamma(t-1) and the
 # G-buffer (64 B) and writes the image and one 20-byte VPL; training reads
@@ -37,7 +39,6 @@ REUSE_R = 2
 # cache) and writes Gamma(t) (16 B)
 BYTES_PER_PIXEL["reuse"] = (64 + 4 + 20) + (64 + 20 + 16)
 BYTES_PER_PIXEL["spp3"] = BYTES_PER_PIXEL["f16"]      # samples never touch memory in the fused pass
-REF_SPP = 256
 # one projected Adam step on FP16 Gamma: Gamma read + write (32 B), the
 # gradient (24 B), m and v each read and written (4 x 24 B in binary32,
 # 4 x 12 B in BF16)
@@ -340,20 +341,75 @@ def with_transparent_texels(g1d, sc, frac, seed):
     return g1m
 
 
-def reference_images(par, sc, fld, g0d, g1d, frames):
-    """256-spp estimates of the same frames by the sampling kernel (own seed,
-    broad initial guide): the reference the 1-spp images' MSE is taken against."""
+def load_truth(name):
+    """FP64 ground truth I(p) stored by tests/golden/make_ground_truth.py (the
+    oracle's cubature of Eq. 1): the rows of tests/golden/<name> as an array."""
+    path = os.path.join(GOLDEN, name)
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    if not rows:
+        raise RuntimeError("%s holds no ground truth" % path)
+    return np.array(rows, dtype=np.float64)
+
+
+class SqErr:
+    """Squared errors of several forms' images against the same reference at
+    the same pixels (on the device, float64): the mean per form and, for a
+    pair of forms, the ratio of their means with its standard error (delta
+    method on the paired samples)."""
+
+    def __init__(self):
+        self.s = {}
+
+    def add(self, name, err):
+        import torch
+        e2 = err.double() ** 2
+        self.s.setdefault(name, []).append(e2)
+
+    def mean(self, name):
+        import torch
+        return float(torch.cat(self.s[name]).mean())
+
+    def ratio(self, num, den):
+        import torch
+        y, x = torch.cat(self.s[num]), torch.cat(self.s[den])
+        my, mx = float(y.mean()), float(x.mean())
+        r = my / mx
+        v = float(((y - my) - r * (x - mx)).pow(2).mean()) / (mx * mx * len(x))
+        return r, v ** 0.5
+
+
+def run_mse_pan(par, sc, fld, g0d, g1d):
+    """Image MSE of each form over frames 30-59 of its own 60-frame run (frames
+    0-59 untimed, fresh guide, seed of rank 0) against the FP64 ground truth
+    at 4096 texels visible in all of those frames."""
     import torch
-    out = {}
+    truth = load_truth("pan_1080p_ground_truth.txt")
+    xw, yw = (torch.from_numpy(truth[:, k].astype(np.int64)).cuda() for k in (0, 1))
+    ref = torch.from_numpy(truth[:, 2]).cuda()
     hw = par.width * par.height
-    for t in frames:
-        gp = make_pass(par, "f32", seed_offset=977, spp=REF_SPP)
+    forms = {"fp32": ("f32", 1, 0), "fp16": ("f16", 1, 0), "bf16": ("bf16", 1, 0),
+             "fp16_reuse": ("f16", 1, REUSE_R), "fp16_3spp": ("f16", 3, 0)}
+    se = SqErr()
+    for name, (dt, spp, radius) in forms.items():
+        gp = make_pass(par, dt, 0, spp=spp, reuse_radius=radius)
         img = torch.empty(hw, dtype=torch.float32, device="cuda")
-        gp.pg_reproject(g0d[t], g1d[t], sc.camera(t), g0d[t])
-        gp.pg_sample(g0d[t], g1d[t], sc.camera(t), fld, 1000003 + t, None, img)
-        out[t] = img
+        for t in range(MSE_RUN_FRAMES):
+            gp.pg_frame(g0d[t], g1d[t], sc.camera(t), g0d[max(t - 1, 0)], fld, t, img)
+            if t in MSE_FRAMES:
+                se.add(name, img[yw * par.width + xw - 2 * t] - ref)
         torch.cuda.synchronize()
+        gp.pg_check()
         gp.close()
+    r16, s16 = se.ratio("fp16", "fp32")
+    rbf, sbf = se.ratio("bf16", "fp32")
+    out = {"frames": [MSE_FRAMES.start, MSE_FRAMES.stop - 1], "run_frames": MSE_RUN_FRAMES,
+           "reference": "FP64 ground truth I(p) (the oracle's cubature of Eq. 1) at %d texels per frame, "
+                        "tests/golden/pan_1080p_ground_truth.txt" % len(truth),
+           "matched_rule": "MSE_fp16 <= 1.02 MSE_fp32"}
+    for name in forms:
+        out[name] = se.mean(name)
+    out.update({"ratio_fp16_over_fp32": r16, "ratio_fp16_over_fp32_se": s16, "matched": bool(r16 <= 1.02),
+                "ratio_bf16_over_fp32": rbf, "ratio_bf16_over_fp32_se": sbf, "matched_bf16": bool(rbf <= 1.02)})
     return out
 
 
@@ -380,13 +436,32 @@ def run_e2e(par, sc, fld, g0h, g1h, gamma_dtype, warmup, steps, seed_offset):
         gp.pg_frames_host(g0h[:warmup], g1h[:warmup], cams[:warmup], fld, 0, img=img_h[:warmup])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        gp.pg_frames_host(g0h[warmup:], g1h[warmup:], cams[warmup:], fld, warmup, g0_prev=g0h[warmup - 1],
-                          img=img_h[warmup:])
+        gp.pg_frames_host(g0h[warmup:warmup + steps], g1h[warmup:warmup + steps], cams[warmup:], fld, warmup,
+                          g0_prev=g0h[warmup - 1], img=img_h[warmup:])
         times.append((time.perf_counter() - t0) * 1e3)
         gp.pg_check()
         gp.close()
     total = sorted(times)[1]
-    return [total / steps] * steps, 2 * hw * 16, hw * 4
+    return [total / steps] * steps, 2 * hw * 16, hw * 4, h2d_link(g0h, g1h, warmup)
+
+
+def h2d_link(g0h, g1h, t):
+    """The host-to-device link in the same run: one frame's two G-buffer planes
+    (the end-to-end leg's upload per frame) copied from page-locked memory by
+    plain cudaMemcpyAsync, back to back on one stream; best of 5 (GB/s)."""
+    import time
+    import torch
+    a, b = torch.empty_like(g0h[t], device="cuda"), torch.empty_like(g1h[t], device="cuda")
+    best = None
+    for _ in range(6):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a.copy_(g0h[t], non_blocking=True)
+        b.copy_(g1h[t], non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return (g0h[t].numel() + g1h[t].numel()) * 4 / best / 1e9
 
 
 def run_4k(par, fld, sc, warmup, steps, flush):
@@ -465,6 +540,56 @@ def run_4k(par, fld, sc, warmup, steps, flush):
             "frame_mpix_s": hw / f / 1e3, "step_mpix_s": hw / (f + g) / 1e3,
             "frame_hbm_frac": BYTES_PER_PIXEL["f16"] * hw / (f * 1e-3) / 1e9 / peak,
             "rejection_rate": sum(rej) / len(rej), "kernels_per_frame": 3}
+
+
+def run_mse_4k(par, fld, sc, n_frames=40):
+    """The gradient-refined form against EM alone at 3840x2160, 4 spp, FP16
+    Gamma: two runs of frames 0..n_frames-1 (untimed, fresh guides, same
+    seed), one with the EM pass alone, one with the EM pass followed by one
+    gradient step per frame (second-moment adjoint over 4 draws, projected
+    Adam with BF16 moments, as the timed leg), each scored by image MSE over
+    frames 24-39 against the FP64 ground truth at 512 fixed pixels."""
+    import torch
+    from paper_2112_09728_gb300.guide import GuidePass
+    truth = load_truth("orbit_4k_ground_truth.txt")
+    hw = par.width * par.height
+    frames = {}
+    for t in range(n_frames):
+        g0, g1, _ = sc.gbuffer_on(t, "cuda")
+        frames[t] = (g0, g1)
+    sel = {}
+    for t in range(n_frames):
+        rows = truth[truth[:, 0] == t]
+        if len(rows):
+            sel[t] = (torch.from_numpy((rows[:, 2] * par.width + rows[:, 1]).astype(np.int64)).cuda(),
+                      torch.from_numpy(rows[:, 3]).cuda())
+    se = SqErr()
+    for name, with_grad in (("em", False), ("em_plus_grad", True)):
+        gp = GuidePass(par.width, par.height, spp=par.spp, gamma_dtype="f16", seed=par.seed, init_pi=par.init_pi,
+                       adam_dtype="bf16")
+        img, loss = torch.empty(hw, device="cuda"), torch.empty(hw, device="cuda")
+        grad = torch.empty((6, hw), device="cuda")
+        for t in range(n_frames):
+            g0, g1 = frames[t]
+            g0p = frames[max(t - 1, 0)][0]
+            gp.pg_frame(g0, g1, sc.camera(t), g0p, fld, t, img)
+            if t in sel:
+                idx, ref = sel[t]
+                se.add(name, img[idx] - ref)
+            if with_grad:
+                gp.pg_grad(g0, g1, sc.camera(t), fld, t, par.spp, loss=loss, grad=grad)
+                gp.pg_adam_step(grad, lr=1e-2, step=t + 1)
+        torch.cuda.synchronize()
+        gp.pg_check()
+        gp.close()
+    del frames
+    r, rs = se.ratio("em_plus_grad", "em")
+    fr = sorted(sel)
+    return {"frames": [fr[0], fr[-1]], "run_frames": n_frames, "pixels_per_frame": len(truth) // len(sel),
+            "reference": "FP64 ground truth I(p) (the oracle's cubature of Eq. 1), "
+                         "tests/golden/orbit_4k_ground_truth.txt",
+            "image_mse_em": se.mean("em"), "image_mse_em_plus_grad": se.mean("em_plus_grad"),
+            "ratio_em_plus_grad_over_em": r, "ratio_se": rs}
 
 
 def run_staged(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush):
@@ -597,14 +722,17 @@ def orbit_step(width, height, frames=4):
     print("orbit step ok: %dx%d, %d frames" % (width, height, frames), file=sys.stderr)
 
 
-def run_diff(width=512, height=512, spp=64, steps=20, lr=1e-2, eval_frames=4, ref_spp=256):
+def run_diff(width=512, height=512, spp=64, steps=20, lr=1e-2, eval_frames=4):
     """Differentiation form against EM at equal samples: two FP32 guides start
     from the same state; one takes `steps` EM steps (the fused pass at `spp`
     samples per pixel), the other `steps` projected-Adam steps on the
     second-moment loss (adjoint over `spp` fresh draws per pixel). Each guide
     is then scored by the estimator's second moment E[F^2] over held-out draws
-    (eval_frames x spp per pixel) and its variance E[F^2] - I^2, with I per
-    pixel from a ref_spp-sample estimate. Steps are timed with CUDA events."""
+    (eval_frames x spp per pixel), its variance E[F^2] - I^2, and the image
+    MSE of eval_frames held-out renders at `spp` samples (staged sampling on a
+    copy of the guide, nothing trained), with I the FP64 ground truth of the
+    workload (one value: every pixel sees the same integrand). Steps are timed
+    with CUDA events."""
     import torch
     from paper_2112_09728_gb300 import scenes
     wl = scenes.workload_diff(width, height, spp, steps)
@@ -615,12 +743,7 @@ def run_diff(width=512, height=512, spp=64, steps=20, lr=1e-2, eval_frames=4, re
     loss = torch.empty(hw, device="cuda")
     grad = torch.empty((6, hw), device="cuda")
     img = torch.empty(hw, device="cuda")
-
-    ref = make_pass(par, "f32", seed_offset=977, spp=ref_spp)
-    ref.pg_reproject(g0, g1, cam, g0)
-    ref.pg_sample(g0, g1, cam, fld, 0, None, img)
-    i2 = img.double() ** 2
-    ref.close()
+    I = float(load_truth("diff_512_ground_truth.txt").reshape(-1)[0])
 
     def score(gp):
         m2 = torch.zeros(hw, dtype=torch.float64, device="cuda")
@@ -628,7 +751,19 @@ def run_diff(width=512, height=512, spp=64, steps=20, lr=1e-2, eval_frames=4, re
             gp.pg_grad(g0, g1, cam, fld, 1000000 + j, spp, loss=loss, grad=grad)
             m2 += loss.double()
         m2 /= eval_frames
-        return {"second_moment": float(m2.mean()), "variance": float((m2 - i2).mean())}
+        # held-out renders of the guide as it stands, each on a fresh copy of
+        # it (reprojection and sampling only: nothing trains)
+        state = gp.pg_get_gamma()
+        mse = 0.0
+        for j in range(eval_frames):
+            r = make_pass(par, "f32", spp=spp)
+            r.pg_set_gamma(state)
+            r.pg_reproject(g0, g1, cam, g0)
+            r.pg_sample(g0, g1, cam, fld, 2000000 + j, None, img)
+            mse += float(((img.double() - I) ** 2).mean())
+            r.close()
+        return {"second_moment": float(m2.mean()), "variance": float(m2.mean()) - I * I,
+                "image_mse": mse / eval_frames}
 
     em, ad = make_pass(par, "f32", spp=spp), make_pass(par, "f32", spp=spp)
     initial = score(em)
@@ -652,9 +787,12 @@ def run_diff(width=512, height=512, spp=64, steps=20, lr=1e-2, eval_frames=4, re
     out = {"workload": "%dx%d, flat Lambertian 0.8, two vMF lobes + 0.05, FP32 Gamma from mu=(0.5,0.5), "
                        "Sigma=0.1 I, pi=0.5; %d samples per pixel per step" % (width, height, spp),
            "steps": steps, "adam_lr": lr, "held_out_samples_per_pixel": eval_frames * spp,
+           "reference": "FP64 ground truth I = %.12g (tests/golden/diff_512_ground_truth.txt)" % I,
            "initial": initial, "em": score(em), "adam": score(ad),
            "em_ms_per_step": sum(a.elapsed_time(b) for a, b in ev_em) / steps,
            "adam_ms_per_step": sum(a.elapsed_time(b) for a, b in ev_ad) / steps}
+    out["image_mse_em"] = out["em"]["image_mse"]
+    out["image_mse_em_plus_grad"] = out["adam"]["image_mse"]
     em.close()
     ad.close()
     return out
@@ -667,13 +805,14 @@ def run_gpu(args, ws, rank, local):
     __graft_entry__.build()
 
     n_frames = args.warmup + args.steps
-    wl = scenes.workload_pan(1920, 1080, frames=n_frames)
+    n_dev = max(n_frames, MSE_RUN_FRAMES)
+    wl = scenes.workload_pan(1920, 1080, frames=n_dev)
     par, fld, sc = wl["params"], wl["field"], wl["scene"]
     hw = par.width * par.height
-    g0h, g1h = upload_frames(sc, n_frames, pin=True)
+    g0h, g1h = upload_frames(sc, n_dev, pin=True)
     g0d, g1d = g0h.cuda(), g1h.cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB of L2
-    keep = set(t for t in MSE_FRAMES if t < n_frames)
+    keep = set()
     torch.cuda.synchronize()
 
     forms = {}
@@ -703,28 +842,19 @@ def run_gpu(args, ws, rank, local):
                       ggx_f0=0.04)[0]
     del g1m
 
-    # matched MSE against a 256-spp reference of frames 30-59
-    mse = None
-    if keep:
-        ref = reference_images(par, sc, fld, g0d, g1d, sorted(keep))
-        m = {}
-        for dt in ("f32", "f16", "bf16", "reuse", "spp3"):
-            acc = 0.0
-            for t in sorted(keep):
-                d = (forms[dt][1][t].double() - ref[t].double())
-                acc += float((d * d).mean())
-            m[dt] = acc / len(keep)
-        mse = {"frames": [min(keep), max(keep)], "reference": "%d spp" % REF_SPP, "fp32": m["f32"],
-               "fp16": m["f16"], "ratio_fp16_over_fp32": m["f16"] / m["f32"],
-               "matched": bool(m["f16"] <= 1.02 * m["f32"]), "fp16_reuse": m["reuse"], "bf16": m["bf16"],
-               "ratio_bf16_over_fp32": m["bf16"] / m["f32"], "fp16_3spp": m["spp3"]}
+    # matched MSE against the FP64 ground truth over frames 30-59 of a
+    # separate 60-frame run of each form
+    mse = run_mse_pan(par, sc, fld, g0d, g1d)
 
-    e2e_ms, h2d, d2h = run_e2e(par, sc, fld, g0h, g1h, "f16", args.warmup, args.steps, rank)
+    e2e_ms, h2d, d2h, link_gbs = run_e2e(par, sc, fld, g0h, g1h, "f16", args.warmup, args.steps, rank)
     del g0h, g1h, g0d, g1d
     w4k = None
     if not args.no_4k:
         wl4 = scenes.workload_4k()
         w4k = run_4k(wl4["params"], wl4["field"], wl4["scene"], 4, 8, flush)
+        w4k["mse"] = run_mse_4k(wl4["params"], wl4["field"], wl4["scene"])
+        w4k["image_mse_em"] = w4k["mse"]["image_mse_em"]
+        w4k["image_mse_em_plus_grad"] = w4k["mse"]["image_mse_em_plus_grad"]
         if rank == 0 and ws == 1 and not args.no_cpu_baseline:
             w4k["cpu_baseline"] = oracle_4k_pixels(wl4["params"], wl4["field"], wl4["scene"], 4, args.cpu_budget / 2)
     diff = None if args.no_diff else run_diff()
@@ -783,8 +913,7 @@ def run_gpu(args, ws, rank, local):
                   "value": res["reuse"]["mpix_s"], "ms_per_step": res["reuse"]["ms_per_step"],
                   "hbm_frac": res["reuse"]["gbs"] / peak,
                   "plain_3spp": {"ms_per_step": res["spp3"]["ms_per_step"],
-                                            "image_mse": mse["fp16_3spp"] if mse else None,
-                                            "reuse_image_mse": mse["fp16_reuse"] if mse else None},
+                                            "image_mse": mse["fp16_3spp"], "reuse_image_mse": mse["fp16_reuse"]},
                   "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL["reuse"]},
         "roofline": {"bound": "hbm", "achieved": main["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": main["gbs"] / peak, "peak_kind": peak_kind,
@@ -796,6 +925,11 @@ def run_gpu(args, ws, rank, local):
         "e2e": {"value": e2e_v, "unit": "Mpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": sum(e2e_ms) / len(e2e_ms),
                 "h2d_gbs": h2d / (sum(e2e_ms) / len(e2e_ms) * 1e-3) / 1e9,
+                "h2d_link_gbs": link_gbs,
+                "link_bound_mpix_s": hw / (h2d / (link_gbs * 1e9)) / 1e6,
+                "frac_of_link_bound": e2e_v / (hw / (h2d / (link_gbs * 1e9)) / 1e6),
+                "link": "one frame's 66 MB G-buffer upload by plain page-locked cudaMemcpyAsync in the same run, "
+                        "best of 5",
                 "api": "pg_frames_host (C ABI, host buffers): page-locked G-buffer uploads and image "
                        "read-backs overlapped with the frames on three streams; wall clock of the call, "
                        "median of three runs; bound by the host-to-device link"},

@@ -332,7 +332,9 @@ pg_status pg_theta_to_gamma(pg_ctx *ctx, const float *d_theta);
  * The work copy of Gamma lives in a fixed 8 MiB device array inside the
  * library, which every GPU that loads the library holds until the process
  * exits. The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture. All
+ * (cudaGetSymbolAddress) and should come before any stream capture; the
+ * address is kept for the life of the process, so after a cudaDeviceReset of
+ * that device the entry point must not be called again. All
  * calls share the array and overwrite it, so calls whose work overlaps on the
  * GPU (different streams, different threads) race: order them on one stream.
  * A non-finite Gamma is not reported (there is no context to hold the flag). */

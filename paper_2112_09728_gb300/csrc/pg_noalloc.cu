@@ -34,8 +34,10 @@ float4* g_work_addr[kMaxDevices] = {};
 int* g_flag_addr[kMaxDevices] = {};
 
 // Device addresses of the scratch on the current device, looked up once per
-// device. In host code the names g_static_work / g_static_flag denote host
-// stand-ins, not device memory, so only these addresses may reach a kernel.
+// device and kept for the life of the process (a cudaDeviceReset of that
+// device would leave them stale; pg.h says so). In host code the names
+// g_static_work / g_static_flag denote host stand-ins, not device memory, so
+// only these addresses may reach a kernel.
 pg_status static_scratch(float4** work, int** flag) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PG_ERR_CUDA;

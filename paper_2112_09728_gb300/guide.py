@@ -327,9 +327,31 @@ def pg_philox(ctr, key, use_curand=False):
 def pg_frame_noalloc(cfg, g0, g1, camera, g0_prev, field, frame, gamma_in, gamma_out, samples, img=None):
     """One staged frame without a context and without device allocation (see
     include/pg.h). gamma_in / gamma_out: uint8 CUDA tensors of the storage
-    layout's size; samples: dict of sample planes (alloc_samples)."""
+    layout's size (H*W*32 bytes for f32, H*W*16 for f16/bf16; the same tensor
+    for an in-place frame); samples: dict of sample planes (alloc_samples:
+    spp*H*W elements each; wx, wy, wz, radiance and strategy required); img:
+    the per-pixel estimate (H*W, or 3*H*W planes for a coloured field) or
+    None. Every size is checked here: the C entry point cannot see the
+    tensors' sizes, and a short buffer would be read and written out of
+    bounds on the device."""
     lib = L.load()
     hw = int(cfg.width) * int(cfg.height)
+    n = int(cfg.spp) * hw
+    gbytes = hw * (32 if int(cfg.gamma_dtype) == L.PG_F32 else 16)
+    checks = [(g0, 4 * hw, "g0"), (g1, 4 * hw, "g1"), (g0_prev, 4 * hw, "g0_prev"),
+              (gamma_in, gbytes, "gamma_in"), (gamma_out, gbytes, "gamma_out")]
+    for k in ("wx", "wy", "wz", "radiance", "strategy"):
+        if samples.get(k) is None:
+            raise ValueError("samples[%r] is required" % k)
+    checks += [(samples[k], n, "samples[%r]" % k) for k in SAMPLE_FLOAT_PLANES + ("strategy",)
+               if samples.get(k) is not None]
+    if img is not None:
+        checks.append((img, GuidePass.image_planes(field) * hw, "img"))
+    for t, want, what in checks:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("%s must be a tensor" % what)
+        if t.numel() != want:
+            raise ValueError("%s must have %d elements, has %d" % (what, want, t.numel()))
     gb = L.pg_gbuffer()
     gb.g0 = _ptr(g0, what="g0", align16=True)
     gb.g1 = _ptr(g1, what="g1", align16=True)
@@ -338,9 +360,6 @@ def pg_frame_noalloc(cfg, g0, g1, camera, g0_prev, field, frame, gamma_in, gamma
     for k in SAMPLE_FLOAT_PLANES:
         setattr(ps, k, _ptr(samples.get(k), what=k))
     ps.strategy = _ptr(samples.get("strategy"), dtype=torch.uint8, what="strategy")
-    for t, n, what in ((g0, 4 * hw, "g0"), (g1, 4 * hw, "g1"), (g0_prev, 4 * hw, "g0_prev")):
-        if t.numel() != n:
-            raise ValueError("%s must have %d elements" % (what, n))
     st = lib.pg_frame_noalloc(C.byref(cfg), C.byref(gb), C.c_void_p(_ptr(g0_prev, what="g0_prev", align16=True)),
                               C.byref(make_field(field)), C.c_uint32(int(frame) & 0xFFFFFFFF),
                               C.c_void_p(_ptr(gamma_in, dtype=torch.uint8, what="gamma_in", align16=True)),
@@ -352,7 +371,7 @@ def pg_frame_noalloc(cfg, g0, g1, camera, g0_prev, field, frame, gamma_in, gamma
 
 
 def planes_to_rows(planes):
-    """[2, HW, 4] raw-moment planes -> [HW, 8] rows (E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, I)."""
+    """[2, HW, 4] raw-moment planes -> [HW, 8] rows (E[X], E[Y], E[X^2], E[Y^2], E[XY], pi, k, W)."""
     return torch.cat([planes[0], planes[1]], dim=1)
 
 

@@ -378,20 +378,26 @@ class QuadScene:
         up = np.cross(right, fwd)
         return Camera(1, pos, tuple(fwd), tuple(right), tuple(up), tan_half_fov=float(self.tan_v))
 
-    def _rays(self, X, cam):
+    def _rays(self, X, cam, xs=None, ys=None):
+        """Primary rays of every pixel [H, W, 3], or of the pixels (xs, ys) [n, 3]
+        (the same arithmetic per pixel)."""
         W, H, m = self.W, self.H, X.m
-        x = (X.arange(W) + 0.5) / W * 2 - 1
-        y = 1 - (X.arange(H) + 0.5) / H * 2
-        sx, sy = X.meshgrid(x * self.tan_v * W / H, y * self.tan_v)
+        if xs is None:
+            x = (X.arange(W) + 0.5) / W * 2 - 1
+            y = 1 - (X.arange(H) + 0.5) / H * 2
+            sx, sy = X.meshgrid(x * self.tan_v * W / H, y * self.tan_v)
+        else:
+            sx = ((X.arr(xs) + 0.5) / W * 2 - 1) * self.tan_v * W / H
+            sy = (1 - (X.arr(ys) + 0.5) / H * 2) * self.tan_v
         f, r, u = X.arr(cam.fwd), X.arr(cam.right), X.arr(cam.up)
         d = f + sx[..., None] * r + sy[..., None] * u
         return d / X.norm(d)
 
-    def _cast(self, X, t):
+    def _cast(self, X, t, xs=None, ys=None):
         m = X.m
         cam = self.camera(t)
         o = X.arr(cam.origin)
-        d = self._rays(X, cam)
+        d = self._rays(X, cam, xs, ys)
         inf = float("inf")
         tg = -o[2] / d[..., 2]
         ground = (d[..., 2] < 0) & (tg > 0)
@@ -456,6 +462,18 @@ class QuadScene:
         _, n_p, d_p, _ = self._cast(X, t - 1)
         g0p = X.f32(X.cat([n_p, d_p[..., None]])).reshape(-1, 4)
         return g0, g1, g0p
+
+    def surface_at(self, t, xs, ys):
+        """(g0, g1) rows of frame t at pixels (xs, ys) only, float32 [n, 4]: the
+        same values as the whole frame's G-buffer at those pixels (g1's motion
+        vectors are left at zero)."""
+        X = _NP()
+        _, n, depth, rough = self._cast(X, t, np.asarray(xs, np.float64), np.asarray(ys, np.float64))
+        g0 = X.f32(X.cat([n, depth[..., None]]))
+        g1 = np.zeros((len(g0), 4), np.float32)
+        g1[:, 2] = rough
+        g1[:, 3] = 0.8
+        return np.ascontiguousarray(g0), g1
 
     def gbuffer(self, t):
         """(g0, g1, g0_prev) of frame t as float32 numpy arrays."""

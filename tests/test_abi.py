@@ -97,3 +97,39 @@ def test_config_default_and_validation_without_gpu(lib):
     assert lib.pg_set_adam_state(None, None, None) == _lib.PG_ERR_ARG
     assert lib.pg_gamma_bytes(None) == 0
     lib.pg_destroy(None)
+
+
+def test_frame_noalloc_binding_checks_every_size_before_the_call():
+    """The C entry point cannot see buffer sizes: the binding refuses a short
+    Gamma, sample plane or image with ValueError before anything reaches the
+    library (CPU tensors suffice, no call is made)."""
+    import torch
+    from paper_2112_09728_gb300 import scenes
+    from paper_2112_09728_gb300.guide import alloc_samples, make_config, pg_frame_noalloc
+
+    W, H = 8, 4
+    hw = W * H
+    cfg = make_config(W, H, spp=2, gamma_dtype="f16")
+    g = torch.zeros(4 * hw)
+    cam, fld = scenes.top_down_camera(), scenes.two_lobe_field(1)
+    ok = dict(g0=g, g1=g, g0_prev=g, gamma_in=torch.zeros(16 * hw, dtype=torch.uint8),
+              gamma_out=torch.zeros(16 * hw, dtype=torch.uint8), samples=alloc_samples(2, hw, device="cpu"),
+              img=torch.zeros(hw))
+
+    def call(**kw):
+        a = dict(ok, **kw)
+        pg_frame_noalloc(cfg, a["g0"], a["g1"], cam, a["g0_prev"], fld, 0, a["gamma_in"], a["gamma_out"],
+                         a["samples"], a["img"])
+
+    bad = [dict(gamma_in=torch.zeros(16 * hw - 16, dtype=torch.uint8)),
+           dict(gamma_out=torch.zeros(32 * hw, dtype=torch.uint8)),          # the FP32 size for an FP16 guide
+           dict(samples=dict(alloc_samples(2, hw, device="cpu"), wx=torch.zeros(hw))),
+           dict(samples=dict(alloc_samples(2, hw, device="cpu"), strategy=torch.zeros(2 * hw - 1, dtype=torch.uint8))),
+           dict(samples={k: v for k, v in alloc_samples(2, hw, device="cpu").items() if k != "radiance"}),
+           dict(img=torch.zeros(hw - 1)), dict(g0_prev=torch.zeros(4 * hw - 4))]
+    for kw in bad:
+        with pytest.raises(ValueError):
+            call(**kw)
+    # sizes right: only then does the binding look at devices (CPU tensors are refused)
+    with pytest.raises(TypeError):
+        call()

@@ -74,3 +74,122 @@ def test_4k_orbit_first_frame_fp16_4spp_sampled_pixels():
     # half vector is good to |dw| <= 1e-6: 5e-4.
     wl = scenes.workload_4k()
     _check(wl, wl["gbuf"](0), img_rtol=5e-4)
+
+
+# ---------------------------------------------------------------------------
+# State-synced parity after the first frame: before each checked frame the
+# oracle gets the GPU's own Gamma(t-1), every pixel of it, so a frame starts
+# from a diverse trained guide, with the screen's rejections and, in the
+# orbit, the frame change of every pixel whose normal moved.
+# ---------------------------------------------------------------------------
+def _gamma_rows(gp, dtype):
+    """The GPU's Gamma as FP64 raw-moment rows [HW, 8] (exact: the storage values)."""
+    raw = host(gp.pg_get_gamma())
+    if dtype == "f32":
+        p = raw.view(np.float32).astype(np.float64).reshape(2, -1, 4)
+        return np.concatenate([p[0], p[1]], 1)
+    from test_gpu_precision import _central_to_raw_moments
+    return _central_to_raw_moments(_records_to_central(raw, dtype))
+
+
+def _gamma_fields(gp, dtype):
+    """The GPU's Gamma in its storage form: raw moments (f32) or mean and central moments."""
+    raw = host(gp.pg_get_gamma())
+    if dtype == "f32":
+        p = raw.view(np.float32).astype(np.float64).reshape(2, -1, 4)
+        return np.concatenate([p[0], p[1]], 1)
+    return _records_to_central(raw, dtype)
+
+
+def _compare_frame(dtype, got_fields, got_img, ref, rimg, margin, idx, img_rtol):
+    ok = margin >= 1e-5
+    assert ok.mean() > 0.98
+    if dtype == "f32":
+        g = got_fields[idx][ok]
+        r = ref[ok]
+        tol = np.array([1e-5] * 5 + [1e-5, 0, 1e-5]) * np.abs(r) + np.array([2e-6] * 5 + [5e-6, 0, 1e-6])
+        assert (np.abs(g - r) <= tol).all(), np.max(np.abs(g - r) / np.maximum(tol, 1e-300))
+    else:
+        r16 = _round(_raw_to_central(ref), dtype)[ok]
+        d = np.abs(got_fields[idx][ok] - r16)
+        floor = np.array([0, 0, 0, 0, 0, 0, 0, 1e-6])
+        assert (d <= 1.01 * _ulp(r16, dtype) + floor).all(), np.max((d - floor) / _ulp(r16, dtype))
+        assert (got_fields[idx][ok, 6] == r16[:, 6]).all()
+    assert close(got_img[idx][ok], rimg[ok], img_rtol, 1e-6) <= 1.0
+
+
+def _synced(wl, dtype, checks, gbuf, grad_step=False, img_rtol=1e-4, extra_cap=None):
+    """Run the workload's frames on the GPU (FP32 or FP16 Gamma; with
+    grad_step one adjoint + projected Adam step after each frame, as the 4K
+    leg of the benchmark), checking each frame of `checks` against the oracle
+    from the GPU's Gamma(t-1) on: the screen's edges, 3000 random pixels, every
+    rejected pixel and (up to extra_cap of them) pixels whose reprojected normal
+    differs from their own."""
+    import torch
+    par, fld = wl["params"], wl["field"]
+    W, H = par.width, par.height
+    hw = W * H
+    gp = guide(par, dtype, adam_dtype="bf16") if grad_step else guide(par, dtype)
+    img = torch.empty(hw, device="cuda")
+    loss, grad = torch.empty(hw, device="cuda"), torch.empty((6, hw), device="cuda")
+    cfg, of = ocfg(par), ofld(fld)
+    rng = np.random.default_rng(17)
+    stats = []
+    for t in range(max(checks) + 1):
+        g0, g1, g0p = gbuf(t)
+        cam = wl["camera"](t)
+        if t in checks:
+            prev = _gamma_rows(gp, dtype)
+        gp.pg_frame(dev(g0), dev(g1), cam, dev(g0p), fld, t, img)
+        if t in checks:
+            gp.pg_check()
+            got, gimg = _gamma_fields(gp, dtype), host(img)     # Gamma(t) as the frame left it
+        if grad_step:
+            gp.pg_grad(dev(g0), dev(g1), cam, fld, t, par.spp, loss=loss, grad=grad)
+            gp.pg_adam_step(grad, lr=1e-2, step=t + 1)
+        if t not in checks:
+            continue
+        _, acc, q = O.reproject(cfg, g0, g1, g0p, prev)
+        moved = (acc == 1) & np.any(g0[:, :3] != g0p[np.maximum(q, 0), :3], 1)
+        _, _, idx = _pixels(W, H, rng)
+        rej = np.nonzero(acc == 0)[0]
+        mv = np.nonzero(moved)[0]
+        if extra_cap is not None and len(mv) > extra_cap:
+            mv = rng.choice(mv, extra_cap, replace=False)
+        idx = np.unique(np.concatenate([idx, rej, mv]))
+        ref, rimg, margin = O.frame_pixels(cfg, ocam(cam), of, t, g0, g1, g0p, prev, idx % W, idx // W)
+        _compare_frame(dtype, got, gimg, ref, rimg, margin, idx, img_rtol)
+        stats.append((t, len(idx), len(rej), int(moved.sum())))
+    gp.close()
+    return stats
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_1080p_pan_frames_1_to_3_state_synced(dtype):
+    wl = scenes.workload_pan(1920, 1080, frames=4)
+    stats = _synced(wl, dtype, (1, 2, 3), wl["gbuf"])
+    # the pan exposes two new columns per frame: every one of them is checked
+    assert all(r == 2 * 1080 for _, _, r, _ in stats)
+
+
+def test_4k_orbit_frames_5_to_7_state_synced_with_gradient_steps():
+    """The benchmark's 4K leg: FP16 Gamma, 4 spp, an EM frame then one adjoint
+    and projected-Adam step (BF16 moments) per frame. Frames 5-7 from the
+    GPU's own state, with the orbit's ~5% rejections (all checked) and its
+    frame changes (20000 of them checked per frame: nearly every pixel's
+    reprojected normal moves: all of the ground and the background)."""
+    import torch
+    wl = scenes.workload_4k()
+    sc = wl["scene"]
+    cache = {}
+
+    def gbuf(t):
+        if t not in cache:
+            cache.clear()
+            cache[t] = tuple(a.cpu().numpy() for a in sc.gbuffer_on(t, "cuda"))
+        return cache[t]
+
+    stats = _synced(wl, "f16", (5, 6, 7), gbuf, grad_step=True, img_rtol=5e-4, extra_cap=20000)
+    for t, n, rej, moved in stats:
+        assert 0.03 < rej / (3840 * 2160) < 0.08
+        assert moved > 0.2 * 3840 * 2160
