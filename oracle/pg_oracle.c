@@ -173,6 +173,19 @@ void or_basis(const double n[3], double t[3], double b[3])
     b[0] = c; b[1] = sg + n[1] * n[1] * a; b[2] = -n[1];
 }
 
+/* The G-buffer's unit normal at g (binary32, unit only to ~6e-8),
+ * normalised in FP64: the local frame is an orthonormal basis about it, so
+ * a direction taken to the world and back is unchanged to FP64 rounding.
+ * (With the binary32 vector as it stands the frame is orthonormal only to
+ * ~6e-8, and a sample re-derived from its world direction moves by that
+ * much: enough, for a GGX mirror reflection of a grazing view, where the half
+ * vector w_o + w_i nearly cancels, to move its weight by percents.) */
+static void unit_normal(const float *g, double n[3])
+{
+    double l = sqrt((double)g[0] * g[0] + (double)g[1] * g[1] + (double)g[2] * g[2]);
+    for (int k = 0; k < 3; ++k) n[k] = g[k] / l;
+}
+
 static void to_world(const double n[3], const double l[3], double w[3])
 {
     double t[3], b[3];
@@ -666,8 +679,9 @@ static int reproject_pixel_s(const or_config *cfg, int x, int y, const float *g0
             memcpy(out, gam_prev + gstride * j, 8 * sizeof(double));
             int same = memcmp(&g0p[4 * j], &g0[4 * i], 3 * sizeof(float)) == 0;
             if (!same) {
-                double np_[3] = {g0p[4 * j], g0p[4 * j + 1], g0p[4 * j + 2]};
-                double nc[3] = {g0[4 * i], g0[4 * i + 1], g0[4 * i + 2]};
+                double np_[3], nc[3];
+                unit_normal(g0p + 4 * j, np_);
+                unit_normal(g0 + 4 * i, nc);
                 frame_change(np_, nc, out);
             }
         }
@@ -741,7 +755,8 @@ static void surface_setup(const or_config *cfg, const or_camera *cam, int x, int
     or_camera_ray(cam, W, H, x, y, o, d);
     double depth = g0[4 * i + 3];
     double wo[3] = {-d[0], -d[1], -d[2]};
-    for (int k = 0; k < 3; ++k) { p->n[k] = g0[4 * i + k]; p->pos[k] = o[k] + depth * d[k]; }
+    unit_normal(g0 + 4 * i, p->n);
+    for (int k = 0; k < 3; ++k) p->pos[k] = o[k] + depth * d[k];
     to_local(p->n, wo, p->wo_l);
     p->rough = g1[4 * i + 2];
     if (!cfg->transparent && is_transparent(p->rough)) p->rough = -1.0;   /* the code is Lambertian then */

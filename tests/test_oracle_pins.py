@@ -676,3 +676,28 @@ def test_adam_first_step_closed_form_and_projection():
     # pixel 2: zero gradient, zero step
     assert np.allclose(th1[2], th0[2], atol=1e-12)
     assert (out[:, 6:] == gam[:, 6:]).all()      # k and W are kept
+
+
+def test_second_moment_gradient_against_central_differences_at_h_1e_4():
+    """The check as the differentiation configuration states it: FP64 central
+    finite differences of the loss with h = 1e-4, the analytic gradient
+    within 1e-3 relative (per component, against the larger of its own
+    magnitude and 1e-3 of the pixel's largest component). h is taken in each
+    parameter's own units: 1 for the mean and pi, 1e-2 for the covariance
+    entries (the guides' variances lie near 1e-2; an absolute 1e-4 there is
+    1% of sigma^2, and the difference's own truncation error, h^2 times the
+    third derivative over 6, is then 3e-3: above the bound whatever the
+    gradient)."""
+    cfg, cam, fld, g0, g1, th = _adjoint_case()
+    n = 32
+    _, grad, _ = O.second_moment(cfg, cam, fld, 3, n, g0, g1, th)
+    fd = np.empty_like(grad)
+    for j, unit in enumerate((1.0, 1.0, 1e-2, 1e-2, 1e-2, 1.0)):
+        h = 1e-4 * unit
+        t1, t2 = th.copy(), th.copy()
+        t1[:, j] += h
+        t2[:, j] -= h
+        fd[:, j] = (O.second_moment(cfg, cam, fld, 3, n, g0, g1, th, t1)[0] -
+                    O.second_moment(cfg, cam, fld, 3, n, g0, g1, th, t2)[0]) / (2 * h)
+    lim = 1e-3 * np.maximum(np.abs(fd), 1e-3 * np.abs(fd).max(1, keepdims=True))
+    assert (np.abs(grad - fd) <= lim).all(), (np.abs(grad - fd) / lim).max()
