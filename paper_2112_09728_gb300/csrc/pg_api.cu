@@ -28,7 +28,7 @@ struct pg_ctx {
     void* adam_v = nullptr;
     float4* vpl = nullptr;    // neighbour reuse: one VPL per sample {world direction, radiance}
     float* vpl_pb = nullptr;  //   and the density of its BRDF draw (0: does not train)
-    float* zbuf = nullptr;    //   and each pixel's rectangle mass Z, from the path-tracing pass
+    float2* hand = nullptr;   //   and each pixel's handover record {Z, reprojection outcome} between the passes
     // pg_frames_host: device rings for the G-buffer and the image, upload and
     // read-back streams, and per-step events (created on first use)
     cudaStream_t hs_up = nullptr, hs_down = nullptr;
@@ -194,7 +194,7 @@ pg_status pg_create(const pg_config* cfg, void* stream, pg_ctx** out) {
         const size_t n = hw * (size_t)cfg->spp;
         e = cudaMalloc(&c->vpl, n * sizeof(float4));
         if (e == cudaSuccess) e = cudaMalloc(&c->vpl_pb, n * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&c->zbuf, hw * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&c->hand, hw * sizeof(float2));
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -294,10 +294,10 @@ pg_status frame_impl(pg_ctx* c, const pg_gbuffer* cur, const float* d_g0_prev, c
     if (c->cfg.reuse_radius > 0) {
         // the paper's two passes: path tracing writes the VPLs, training reads them
         e = pgk::launch_pt(c->cfg.gamma_dtype, P, c->gam[c->cur], g0, g1, g0p, d_img, frame, c->vpl, c->vpl_pb,
-                           c->zbuf, c->d_err, c->stream);
+                           c->hand, c->d_err, c->stream);
         if (e == cudaSuccess)
             e = pgk::launch_train(c->cfg.gamma_dtype, P, c->gam[c->cur], c->gam[c->cur ^ 1], g0, g1, g0p, frame,
-                                  c->vpl, c->vpl_pb, c->zbuf, c->d_err, c->stream);
+                                  c->vpl, c->vpl_pb, c->hand, c->d_err, c->stream);
     } else {
         e = pgk::launch_frame(c->cfg.gamma_dtype, P, c->gam[c->cur], c->gam[c->cur ^ 1], g0, g1, g0p, d_img, frame,
                               c->d_err, c->stream);
@@ -591,7 +591,7 @@ void pg_destroy(pg_ctx* c) {
     if (c->adam_v) cudaFree(c->adam_v);
     if (c->vpl) cudaFree(c->vpl);
     if (c->vpl_pb) cudaFree(c->vpl_pb);
-    if (c->zbuf) cudaFree(c->zbuf);
+    if (c->hand) cudaFree(c->hand);
     if (c->hs_up) cudaStreamSynchronize(c->hs_up);
     if (c->hs_down) cudaStreamSynchronize(c->hs_down);
     release_host(c);

@@ -37,6 +37,48 @@ static __device__ __forceinline__ bool reproject_pixel(const Params& P, int x, i
     return false;
 }
 
+// Reprojection with a record of its outcome for a later pass (neighbour reuse):
+// 0xFFFFFFFF for a re-initialised pixel, else the previous pixel j, with bit 31
+// set when the normals differ and the guide went through the frame change.
+template <int DT>
+static __device__ __forceinline__ bool reproject_pixel_rec(const Params& P, int x, int y, float4 a0, float4 a1,
+                                                    const void* __restrict__ gin, const float4* __restrict__ g0p,
+                                                    size_t hw, Gam& g, uint32_t& rec, int* err) {
+    float4 gp;
+    const int j = reproject_index(P, x, y, a0, a1, g0p, &gp, err);
+    rec = 0xFFFFFFFFu;
+    if (j < 0) {
+        g = init_gam(P);
+        return true;
+    }
+    g = Store<DT>::load(gin, hw, (size_t)j);
+    rec = (uint32_t)j;
+    if (!same_normal(gp, a0)) {
+        change_frame(g, make_float3(gp.x, gp.y, gp.z), make_float3(a0.x, a0.y, a0.z));
+        rec |= 0x80000000u;
+    }
+    return false;
+}
+
+// The same guide again from the record: the outcome is not re-derived, only
+// the guide reloaded (and the frame change redone where bit 31 says so).
+template <int DT>
+static __device__ __forceinline__ bool replay_reprojection(const Params& P, uint32_t rec, float4 a0,
+                                                    const void* __restrict__ gin, const float4* __restrict__ g0p,
+                                                    size_t hw, Gam& g, int* err) {
+    const int j = (int)(rec & 0x7FFFFFFFu);
+    if (rec == 0xFFFFFFFFu || !PG_IN_BOUNDS(j, hw, err)) {
+        g = init_gam(P);
+        return true;
+    }
+    g = Store<DT>::load(gin, hw, (size_t)j);
+    if (rec & 0x80000000u) {
+        const float4 gp = __ldcs(g0p + j);
+        change_frame(g, make_float3(gp.x, gp.y, gp.z), make_float3(a0.x, a0.y, a0.z));
+    }
+    return false;
+}
+
 static inline dim3 grid_for(const Params& P) {
     const size_t hw = (size_t)P.W * P.H;
     return dim3((unsigned)((hw + kBlock - 1) / kBlock));

@@ -15,9 +15,12 @@ constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kInv2Pi = 0.159154943091895335769f;
 constexpr float kInv4Pi2 = 0.0253302959105844428f;   // 1 / (4 pi^2)
 constexpr float k4OverPi = 1.27323954473516268615f;
-// Gauss-Legendre tiers for the Phi_2 correction: 4 nodes for |rho| <= 0.6,
-// 6 for |rho| <= 0.75, 8 above (each keeps a corner's error near 1e-8 or below)
-constexpr int kGLTotal = 4 + 6 + 8;
+// Gauss-Legendre nodes of the Phi_2 correction: one 8-node rule, whose
+// corner error stays near 1e-8 or below up to |rho| = 0.9, for every pixel.
+// (Fewer nodes would do for small |rho|, but pixels of one warp on different
+// rules run each rule's nodes in turn: on trained guides a warp then ran 11
+// to 14 node steps where one common rule runs 8.)
+constexpr int kGLNodes = 8;
 
 enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 
@@ -63,9 +66,8 @@ struct Params {
     // channels (lobe_scale and field_const then hold the luminance)
     int rgb;
     float lobe_rgb[8][3], field_const_rgb[3];
-    // Gauss-Legendre rules on [-1, 1] with 4, 6 and 8 nodes, back to back
-    // (computed on the host at context creation)
-    float gl_x[kGLTotal], gl_w[kGLTotal];
+    // the Gauss-Legendre rule on [-1, 1] (computed on the host at context creation)
+    float gl_x[kGLNodes], gl_w[kGLNodes];
     // neighbour-VPL reuse: window radius (0 = off), number of candidates
     // ((2R+1)^2 - 1) spp, and the stride of the walk through them
     int reuse_r, reuse_c, reuse_stride;
@@ -187,23 +189,36 @@ __device__ __forceinline__ float3 square_to_hemi(float u, float v) {
     return make_float3(dx * lift, dy * lift, z);
 }
 
+// (4/pi) atan(t) for t in [-1, 1]: t P(t^2) with P of degree 7, this
+// library's own fit (fit_atan.py; absolute error 5e-8, 1.7e-7 in binary32).
+__device__ __forceinline__ float atan_unit(float t) {
+    const float t2 = t * t;
+    float p = -5.160561652e-03f;
+    p = fmaf(p, t2, 2.782882500e-02f);
+    p = fmaf(p, t2, -7.117607943e-02f);
+    p = fmaf(p, t2, 1.227560273e-01f);
+    p = fmaf(p, t2, -1.770841680e-01f);
+    p = fmaf(p, t2, 2.539659938e-01f);
+    p = fmaf(p, t2, -4.243687760e-01f);
+    p = fmaf(p, t2, 1.273238691e+00f);
+    return p * t;
+}
+
 // Inverse map: disk point d = w_xy / sqrt(1 + z); the dominant disk axis gives
-// the square coordinate of radius |d|, the other one follows from atan of the
-// component ratio (within [-pi/4, pi/4]).
+// the square coordinate of radius |d|, the other one follows from the
+// arctangent of the component ratio (within [-1, 1]), for either axis by the
+// same instructions.
 __device__ __forceinline__ float2 hemi_to_square(float3 w) {
     const float z = fmaxf(w.z, 0.0f);
     const float inv = rsqrtf(1.0f + z);
     const float dx = w.x * inv, dy = w.y * inv;
     const float r = sqrtf(dx * dx + dy * dy);
     if (r < 1e-30f) return make_float2(0.5f, 0.5f);   // the pole (to within 1e-30)
-    float a, b;
-    if (fabsf(dx) >= fabsf(dy)) {
-        a = copysignf(r, dx);
-        b = a * k4OverPi * atanf(__fdividef(dy, dx));
-    } else {
-        b = copysignf(r, dy);
-        a = b * k4OverPi * atanf(__fdividef(dx, dy));
-    }
+    const bool xdom = fabsf(dx) >= fabsf(dy);
+    const float lead = xdom ? dx : dy, other = xdom ? dy : dx;
+    const float m = copysignf(r, lead);                 // the dominant coordinate
+    const float n = m * atan_unit(__fdividef(other, lead));
+    const float a = xdom ? m : n, b = xdom ? n : m;
     return make_float2(0.5f * (a + 1.0f), 0.5f * (b + 1.0f));
 }
 
@@ -255,6 +270,8 @@ template <typename H>
 struct HalfStore {
     static __device__ __forceinline__ float cvt(uint16_t v);
     static __device__ __forceinline__ uint16_t pack(float v);
+    // two fields at once, lo in the low half: the same rounding as pack
+    static __device__ __forceinline__ uint32_t pack2(float lo, float hi);
 };
 template <>
 __device__ __forceinline__ float HalfStore<__half>::cvt(uint16_t v) { return __half2float(__ushort_as_half(v)); }
@@ -266,6 +283,14 @@ template <>
 __device__ __forceinline__ uint16_t HalfStore<__half>::pack(float v) {
     return __half_as_ushort(__float2half_rn(fminf(fmaxf(v, -65504.0f), 65504.0f)));
 }
+// the pair conversion with saturation to the largest finite value: for a
+// finite input the same bits as the clamp-then-round of pack
+template <>
+__device__ __forceinline__ uint32_t HalfStore<__half>::pack2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
 template <>
 __device__ __forceinline__ float HalfStore<__nv_bfloat16>::cvt(uint16_t v) {
     return __bfloat162float(__ushort_as_bfloat16(v));
@@ -273,6 +298,12 @@ __device__ __forceinline__ float HalfStore<__nv_bfloat16>::cvt(uint16_t v) {
 template <>
 __device__ __forceinline__ uint16_t HalfStore<__nv_bfloat16>::pack(float v) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <>
+__device__ __forceinline__ uint32_t HalfStore<__nv_bfloat16>::pack2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
 // Stochastic rounding of a binary32 value to the storage type, from 16
@@ -321,11 +352,9 @@ struct Store16 {
         return g;
     }
     static __device__ __forceinline__ void store(void* base, size_t, size_t i, const Gam& g) {
-        auto pk = [](float lo, float hi) {
-            return (uint32_t)HalfStore<H>::pack(lo) | ((uint32_t)HalfStore<H>::pack(hi) << 16);
-        };
         __stcs(reinterpret_cast<uint4*>(base) + i,
-               make_uint4(pk(g.ex, g.ey), pk(g.sxx, g.syy), pk(g.sxy, g.pi), pk(g.k, g.W)));
+               make_uint4(HalfStore<H>::pack2(g.ex, g.ey), HalfStore<H>::pack2(g.sxx, g.syy),
+                          HalfStore<H>::pack2(g.sxy, g.pi), HalfStore<H>::pack2(g.k, g.W)));
     }
     // stochastic rounding: field j takes the 16 bits (r[j / 2] >> 16 (j mod 2)) & 0xFFFF
     static __device__ __forceinline__ void store_sr(void* base, size_t, size_t i, const Gam& g, uint4 r) {
@@ -496,8 +525,8 @@ __device__ __forceinline__ float normal_tail(float h) {
 // Z by four corners of the bivariate normal cdf in the Drezner-Wesolowsky form
 //   Phi_2(h,k;rho) = Phi(h)Phi(k) + 1/(2 pi) int_0^asin(rho) exp(-(h^2+k^2-2hk sin t)/(2 cos^2 t)) dt,
 // so Z = (Phi(h1)-Phi(h0)) (Phi(k1)-Phi(k0)) + signed sum of the four corner
-// integrals, each by a Gauss-Legendre rule in t of 4, 6 or 8 nodes chosen by
-// |rho| (abs. error ~1e-8 up to |rho| = 0.9). As (h^2+k^2-2hks)/cos^2 t >=
+// integrals, each by the 8-node Gauss-Legendre rule in t (abs. error ~1e-8
+// up to |rho| = 0.9). As (h^2+k^2-2hks)/cos^2 t >=
 // max(h^2, k^2), and >= h^2 + k^2 when hk rho <= 0, a corner whose bound
 // exceeds 36 contributes below e^-18 (times asin(rho)/(2 pi) < 0.18) and is
 // skipped.
@@ -517,9 +546,6 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
     const bool c00 = live(h0, k0, h0s, k0s), c10 = live(h1, k0, h1s, k0s);
     const bool c01 = live(h0, k1, h0s, k1s), c11 = live(h1, k1, h1s, k1s);
     if (rho != 0.0f && (c00 || c10 || c01 || c11)) {
-        const float ar = fabsf(rho);
-        const int first = ar <= 0.6f ? 0 : (ar <= 0.75f ? 4 : 10);
-        const int last = ar <= 0.6f ? 4 : (ar <= 0.75f ? 10 : kGLTotal);
         const float asr = asinf(rho), half = 0.5f * asr;
         // exponent of corner (h, k) in base 2: (2hk s - h^2 - k^2) log2(e) / (2 cos^2 t)
         const float l2 = 0.72134752044448170f;                  // log2(e) / 2
@@ -528,7 +554,8 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
         const float a10 = (h1s + k0s) * l2, b10 = 2.0f * h1 * k0 * l2;
         const float a01 = (h0s + k1s) * l2, b01 = 2.0f * h0 * k1 * l2;
         float acc = 0.0f;
-        for (int i = first; i < last; ++i) {
+#pragma unroll
+        for (int i = 0; i < kGLNodes; ++i) {
             const float s = sin_small(fmaf(half, P.gl_x[i], half));
             const float q = __fdividef(1.0f, fmaf(-s, s, 1.0f));     // 1 / cos^2 t, cos^2 t >= 0.19
             float v = 0.0f;
@@ -647,6 +674,39 @@ __device__ __forceinline__ Surf make_surf(const Params& P, int x, int y, float4 
     return s;
 }
 
+// GGX f_r cos(theta_i) and its draw's density at local wi, from the cosines
+// of the unit half vector h: ct = n.h, st2 = 1 - (n.h)^2, oh = w_o.h (> 0).
+// With D = a^2 / (pi t^2), t = a^2 ct^2 + st2 (= (n.h)^2 (a^2 - 1) + 1, free
+// of cancellation), Smith's G1(w_i) = 2 c / e, e = c + sqrt(a^2 + (1 - a^2) c^2):
+//   f_r cos = D G1(w_i) go F,  p_b = D ct / (4 oh),
+// both through one reciprocal r = 1 / (pi t^2 e oh).
+__device__ __forceinline__ void ggx_eval(const Surf& s, float wiz, float ct, float st2, float oh, float& fcos,
+                                         float& pb, float f0) {
+    const float t = fmaf(s.a2, ct * ct, st2);
+    const float e = wiz + sqrtf(fmaf(1.0f - s.a2, wiz * wiz, s.a2));
+    const float den = kPi * t * t * e * oh;
+    const float r = den > 1e-30f ? __fdividef(1.0f, den) : __fdiv_rn(1.0f, den);
+    const float a2r = s.a2 * r;
+    fcos = a2r * 2.0f * wiz * oh * s.go;
+    if (f0 < 1.0f) {
+        const float m = 1.0f - oh, m2 = m * m;
+        fcos *= fmaf(1.0f - f0, m2 * m2 * m, f0);
+    }
+    pb = a2r * ct * e * 0.25f;
+}
+
+// The half vector's cosines of a direction pair: h = w_o + w_i normalised.
+// (Near a grazing mirror pair w_i ~ -w_o reflected, h's components cancel in
+// binary32: a direction the GGX sampler drew carries its own h instead.)
+__device__ __forceinline__ void half_cosines(const Surf& s, float3 wi, float& ct, float& st2, float& oh) {
+    const float3 h = make_float3(s.wo.x + wi.x, s.wo.y + wi.y, s.wo.z + wi.z);
+    const float hz2 = h.z * h.z, hxy2 = h.x * h.x + h.y * h.y, hl2 = hz2 + hxy2;
+    const float ihl = rsqrtf(hl2);
+    ct = h.z * ihl;
+    st2 = hxy2 * ihl * ihl;
+    oh = dot3(s.wo, h) * ihl;
+}
+
 // f_r cos(theta_i) and the BRDF draw's density (per steradian) at local wi.
 // f0: Schlick reflectance of the GGX lobe at normal incidence (1: F = 1).
 __device__ __forceinline__ void brdf_eval(const Surf& s, float3 wi, float& fcos, float& pb, float f0) {
@@ -660,24 +720,14 @@ __device__ __forceinline__ void brdf_eval(const Surf& s, float3 wi, float& fcos,
         fcos = s.wo.z > 0.0f ? s.albedo * pb : 0.0f;
         return;
     }
-    if (!(s.wo.z > 0.0f)) {
+    float ct, st2, oh;
+    half_cosines(s, wi, ct, st2, oh);
+    if (!(s.wo.z > 0.0f) || !(oh > 0.0f)) {
         fcos = 0.0f;
         pb = 0.0f;
         return;
     }
-    const float3 h = make_float3(s.wo.x + wi.x, s.wo.y + wi.y, s.wo.z + wi.z);
-    const float hz2 = h.z * h.z, hxy2 = h.x * h.x + h.y * h.y, hl2 = hz2 + hxy2;
-    // (n.h)^2 (a^2 - 1) + 1 = (a^2 h_z^2 + h_x^2 + h_y^2) / |h|^2, free of cancellation
-    const float t = fdiv(fmaf(s.a2, hz2, hxy2), hl2);   // in [a^2, 1]
-    const float D = __fdividef(s.a2, kPi * t * t);
-    const float ihl = rsqrtf(hl2);
-    const float nh = h.z * ihl, oh = dot3(s.wo, h) * ihl;
-    fcos = D * smith_g1(s.a2, wi.z) * s.go;
-    if (f0 < 1.0f) {
-        const float m = 1.0f - oh, m2 = m * m;
-        fcos *= fmaf(1.0f - f0, m2 * m2 * m, f0);
-    }
-    pb = oh > 0.0f ? fdiv(D * nh, 4.0f * oh) : 0.0f;
+    ggx_eval(s, wi.z, ct, st2, oh, fcos, pb, f0);
 }
 
 // The draw of a transparent surface: reflection when x1 < F, refraction (into
@@ -697,21 +747,26 @@ __device__ __forceinline__ bool glass_sample(const Surf& s, float x1, float3& wi
     return true;
 }
 
-// BRDF draw from two uniforms (Lambertian or GGX); false for a wasted draw
-// (below the horizon).
-__device__ __forceinline__ bool brdf_sample(const Surf& s, float x1, float x2, float3& wi) {
-    float sn, cs;
-    sincos_turn(x2, &sn, &cs);
+// BRDF draw from a uniform x1 and the sine and cosine of a uniform turn x2
+// (Lambertian or GGX); false for a wasted draw (below the horizon). A GGX
+// draw also returns its half vector's cosines ct = n.h, st2 = 1 - (n.h)^2
+// and oh = w_o.h, with which it is evaluated (see half_cosines).
+__device__ __forceinline__ bool brdf_sample_sc(const Surf& s, float x1, float sn, float cs, float3& wi, float& hct,
+                                               float& hst2, float& hoh) {
     if (s.mat == MAT_LAMBERT) {
         const float r = sqrtf(x1);
         wi = make_float3(r * cs, r * sn, sqrtf(1.0f - x1));
         return true;
     }
     const float id = __fdividef(1.0f, (1.0f - x1) + s.a2 * x1);
-    const float ct = sqrtf((1.0f - x1) * id), st = sqrtf(s.a2 * x1 * id);
+    const float st2 = s.a2 * x1 * id;
+    const float ct = sqrtf((1.0f - x1) * id), st = sqrtf(st2);
     const float3 h = make_float3(st * cs, st * sn, ct);
     const float oh = dot3(s.wo, h);
     wi = make_float3(2.0f * oh * h.x - s.wo.x, 2.0f * oh * h.y - s.wo.y, 2.0f * oh * h.z - s.wo.z);
+    hct = ct;
+    hst2 = st2;
+    hoh = oh;
     return oh > 0.0f && wi.z > 0.0f;
 }
 
@@ -765,6 +820,8 @@ struct Smp {
     int strat;        // ST_* | ST_INVALID
     float3 Lrgb;      // coloured fields: the radiance's channels
     float wgt;        // coloured fields: the estimate per unit radiance (F = wgt L per channel)
+    bool hs;          // a GGX BRDF draw: its half vector's cosines hct, hst2, hoh
+    float hct, hst2, hoh;
 };
 
 template <bool RGB = false>
@@ -786,7 +843,18 @@ __device__ __forceinline__ void eval_sample(const Params& P, const Guide& d, con
         return;
     }
     float fr;
-    brdf_eval(s, o.wl, fr, o.pb, P.f0);
+    if (s.mat == MAT_GGX && o.wl.z > 0.0f && s.wo.z > 0.0f) {
+        // the draw's own half vector, or w_o + w_i for a direction the guide drew
+        if (!o.hs) half_cosines(s, o.wl, o.hct, o.hst2, o.hoh);
+        if (o.hoh > 0.0f) {
+            ggx_eval(s, o.wl.z, o.hct, o.hst2, o.hoh, fr, o.pb, P.f0);
+        } else {
+            fr = 0.0f;
+            o.pb = 0.0f;
+        }
+    } else {
+        brdf_eval(s, o.wl, fr, o.pb, P.f0);
+    }
     o.fcos = o.L * fr;
     if (!have_u) {
         const float2 u = hemi_to_square(o.wl);
@@ -819,16 +887,18 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
     Smp o;
     const uint4 r0 = philox4x32_10(make_uint4(pix, frame, si, stream0), P.rk);
     const float zeta = unit24(r0.x);
-    bool have_u = false, valid;
+    bool have_u = false, valid = false, brdf = false;
+    o.hs = false;
+    // word 2's turn is the Box-Muller angle of a guide draw and the azimuth of
+    // a BRDF draw: one sincos serves the lanes of either strategy
+    float sn, cs, x1 = unit24(r0.y);
+    sincos_turn(unit24(r0.z), &sn, &cs);
     if (s.mat == MAT_GLASS) {
         // a transparent surface (always gated): one of its two deltas
         o.strat = ST_DELTA;
-        valid = glass_sample(s, unit24(r0.y), o.wl);
+        valid = glass_sample(s, x1, o.wl);
     } else if (zeta < d.pi_eff) {
-        const float x1 = unit24_open0(r0.y), x2 = unit24(r0.z);
-        const float rr = sqrtf(-2.0f * __logf(x1));
-        float sn, cs;
-        sincos_turn(x2, &sn, &cs);
+        const float rr = sqrtf(-2.0f * __logf(unit24_open0(r0.y)));
         const float z1 = rr * cs, z2 = rr * sn;
         o.ux = fmaf(d.l11, z1, d.mx);
         o.uy = fmaf(d.l22, z2, fmaf(d.l21, z1, d.my));
@@ -842,11 +912,18 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
             // fresh uniforms from bits the draw has not used: word 3 and the
             // low bytes of words 0-2 (independent of their top 24 bits)
             const uint32_t spare = (r0.x & 0xFFu) | ((r0.y & 0xFFu) << 8) | ((r0.z & 0xFFu) << 16);
-            valid = brdf_sample(s, unit24(r0.w), (float)spare * 5.9604644775390625e-8f, o.wl);
+            x1 = unit24(r0.w);
+            sincos_turn((float)spare * 5.9604644775390625e-8f, &sn, &cs);
+            brdf = true;
         }
     } else {
         o.strat = ST_BRDF;
-        valid = brdf_sample(s, unit24(r0.y), unit24(r0.z), o.wl);
+        brdf = true;
+    }
+    // the BRDF draw of both the BRDF strategy and a fallback, at one site
+    if (brdf) {
+        valid = brdf_sample_sc(s, x1, sn, cs, o.wl, o.hct, o.hst2, o.hoh);
+        o.hs = s.mat == MAT_GGX;
     }
     if (!valid) o.strat |= ST_INVALID;
     eval_sample<RGB>(P, d, s, o, have_u);
@@ -930,8 +1007,18 @@ struct Stats {
         const float2 u = hemi_to_square(wl);
         const float pg = guide_pdf(d, u.x, u.y);
         const float pmix = d.pi_eff * pg + (1.0f - d.pi_eff * d.Z) * pb;
-        const float w = fdiv(L * fr, pb_src);
-        const float gam = pmix > 0.0f ? fdiv(d.pi_eff * pg, pmix) : 0.0f;
+        // w = L f_r / p_src and gamma = pi p_g / p_mix through one reciprocal
+        // of p_src p_mix while that product is a normal number
+        const float den = pb_src * pmix;
+        float w, gam;
+        if (den > 1e-30f && den < 1e30f) {
+            const float r = __fdividef(1.0f, den);
+            w = L * fr * pmix * r;
+            gam = d.pi_eff * pg * pb_src * r;
+        } else {
+            w = fdiv(L * fr, pb_src);
+            gam = pmix > 0.0f ? fdiv(d.pi_eff * pg, pmix) : 0.0f;
+        }
         add(g, w, gam, u.x, u.y);
     }
     __device__ __forceinline__ void add(const Gam& g, float w, float gam, float ux, float uy) {
@@ -981,11 +1068,15 @@ __device__ __forceinline__ void m_step(const Params& P, Gam& g, const Stats& st)
     const float B = fmaf(eta, b, e1 * m0);
     if (a > 0.0f && A > 0.0f) {
         // lambda delta = eta S1 / A and lambda M2 = eta S2 / A: bounded ratios,
-        // formed without a reciprocal of a or A (either may be subnormal)
-        const float lam = fdiv(eta * a, A), l1 = 1.0f - lam;
-        const float ldx = fdiv(eta * st.s1x.s, A), ldy = fdiv(eta * st.s1y.s, A);
-        const float lmxx = fdiv(eta * st.s2xx.s, A), lmyy = fdiv(eta * st.s2yy.s, A);
-        const float lmxy = fdiv(eta * st.s2xy.s, A);
+        // by one hardware reciprocal of A while A is normal (2 ulp, as fdiv's
+        // fast path), by correctly rounded divisions for a subnormal A
+        const bool fast = A > 1e-30f;
+        const float rA = __fdividef(1.0f, fast ? A : 1.0f);
+        auto byA = [&](float v) { return fast ? v * rA : __fdiv_rn(v, A); };
+        const float lam = byA(eta * a), l1 = 1.0f - lam;
+        const float ldx = byA(eta * st.s1x.s), ldy = byA(eta * st.s1y.s);
+        const float lmxx = byA(eta * st.s2xx.s), lmyy = byA(eta * st.s2yy.s);
+        const float lmxy = byA(eta * st.s2xy.s);
         g.sxx = fmaf(l1, g.sxx, fmaf(-ldx, ldx, lmxx));
         g.syy = fmaf(l1, g.syy, fmaf(-ldy, ldy, lmyy));
         g.sxy = fmaf(l1, g.sxy, fmaf(-ldx, ldy, lmxy));

@@ -19,12 +19,13 @@ cudaError_t launch_init(int dt, const Params& P, void* gam, float init_pi, cudaS
 cudaError_t launch_frame(int dt, const Params& P, const void* gin, void* gout, const float4* g0,
                          const float4* g1, const float4* g0p, float* img, uint32_t frame, int* err,
                          cudaStream_t st);
-// neighbour-VPL reuse: the path-tracing pass (writes the VPL buffer) and the training pass
+// neighbour-VPL reuse: the path-tracing pass (writes the VPL buffer and each pixel's handover
+// record {Z, reprojection outcome}) and the training pass (reads both)
 cudaError_t launch_pt(int dt, const Params& P, const void* gin, const float4* g0, const float4* g1,
-                      const float4* g0p, float* img, uint32_t frame, float4* vpl, float* pb_src, float* zbuf,
+                      const float4* g0p, float* img, uint32_t frame, float4* vpl, float* pb_src, float2* hand,
                       int* err, cudaStream_t st);
 cudaError_t launch_train(int dt, const Params& P, const void* gin, void* gout, const float4* g0, const float4* g1,
-                         const float4* g0p, uint32_t frame, const float4* vpl, const float* pb_src, const float* zbuf,
+                         const float4* g0p, uint32_t frame, const float4* vpl, const float* pb_src, const float2* hand,
                          int* err, cudaStream_t st);
 cudaError_t launch_reproject(int dt, const Params& P, const void* gin, float4* work, const float4* g0,
                              const float4* g1, const float4* g0p, uint8_t* accept, int* err, cudaStream_t st);

@@ -117,9 +117,7 @@ void config_params(const pg_config& cfg, Params& P) {
     P.init_c[0] = cfg.init_sigma[0];
     P.init_c[1] = cfg.init_sigma[1];
     P.init_c[2] = cfg.init_sigma[2];
-    gauss_legendre(4, P.gl_x, P.gl_w);
-    gauss_legendre(6, P.gl_x + 4, P.gl_w + 4);
-    gauss_legendre(8, P.gl_x + 10, P.gl_w + 10);
+    gauss_legendre(pgk::kGLNodes, P.gl_x, P.gl_w);
     // neighbour reuse: C candidates, walked with the smallest stride >= 0.618 C
     // that is coprime with C (so N <= C picks are distinct)
     P.sr = cfg.stochastic_round;

@@ -1,8 +1,9 @@
 // Neighbour-VPL reuse (Sec. 3.2, 4.2): the frame as the paper's two passes.
 // k_pt reprojects, samples and writes one VPL per sample (world direction,
-// radiance and, for a BRDF-strategy draw, its BRDF density) plus Z per pixel;
-// k_train reprojects again and trains each pixel's guide on its own samples
-// and N picks among its window's samples.
+// radiance and, for a BRDF-strategy draw, its BRDF density), and per pixel a
+// handover record {Z, outcome of the reprojection}; k_train takes the
+// reprojected guide from that record (no second reprojection) and trains it
+// on its own samples and N picks among its window's samples.
 #include "pg_common.cuh"
 
 namespace pgk {
@@ -13,13 +14,14 @@ namespace {
 // and image as in k_frame, plus one VPL per sample in the buffer Pi: world
 // direction and radiance in vpl, and in pb_src the density of the pixel's
 // BRDF draw for a BRDF-strategy sample (0 for samples that do not train).
-// The guide's rectangle mass Z goes to zbuf for the training pass.
+// Each pixel's handover record, {Z, reprojection record}, goes to hand for
+// the training pass (reproject_pixel_rec).
 template <int DT, bool ONE, bool RGB>
 __global__ void __launch_bounds__(kBlock, 5) k_pt(const Params P, const void* __restrict__ gin,
                                                   const float4* __restrict__ g0, const float4* __restrict__ g1,
                                                   const float4* __restrict__ g0p, float* __restrict__ img,
                                                   uint32_t frame, float4* __restrict__ vpl,
-                                                  float* __restrict__ pb_src, float* __restrict__ zbuf,
+                                                  float* __restrict__ pb_src, float2* __restrict__ hand,
                                                   int* __restrict__ err) {
     const size_t hw = (size_t)P.W * P.H;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -27,10 +29,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_pt(const Params P, const void* __
     const int y = i / P.W, x = i - y * P.W;
     const float4 a0 = __ldcs(g0 + i), a1 = __ldcs(g1 + i);
     Gam g;
-    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g, err);
+    uint32_t rec;
+    const bool reinit = reproject_pixel_rec<DT>(P, x, y, a0, a1, gin, g0p, hw, g, rec, err);
     const Surf s = make_surf(P, x, y, a0, a1);
     const Guide d = derive_guide(P, g, gated(P, reinit, a1));
-    zbuf[i] = d.Z;
+    hand[i] = make_float2(d.Z, __uint_as_float(rec));
     Kahan f, fr, fg, fb;
     const int spp = ONE ? 1 : P.spp;
     for (int si = 0; si < spp; ++si) {
@@ -70,8 +73,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_pt(const Params P, const void* __
 // BRDF-strategy VPLs and N picks of its window, each weighted f / p_src, then
 // the M-step. N = 5 + floor(15 (k_max - k) / k_max) (at most the window's C
 // candidates); the picks walk the candidates from a Philox start by a stride
-// coprime with C, so they are distinct. Reprojection is recomputed (same
-// inputs, same result as pass 1) rather than stored; Z comes from pass 1.
+// coprime with C, so they are distinct. The reprojected guide and Z come
+// from pass 1's handover record.
 //
 // Each thread first classifies its N picks in a loop of the same length on
 // every lane (decode, on screen, drawn by the BRDF strategy), keeping a bit
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
                                                      const float4* __restrict__ g0p, uint32_t frame,
                                                      const float4* __restrict__ vpl,
                                                      const float* __restrict__ pb_src,
-                                                     const float* __restrict__ zbuf, int* __restrict__ err) {
+                                                     const float2* __restrict__ hand, int* __restrict__ err) {
     const size_t hw = (size_t)P.W * P.H;
     const int spp = ONE ? 1 : P.spp;
     int x, y;
@@ -136,11 +139,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
     if (!inside) return;
     const int i = y * P.W + x;
     const float4 a0 = __ldcs(g0 + i), a1 = __ldcs(g1 + i);
+    const float2 hv = __ldcs(hand + i);
     Gam g;
-    const bool reinit = reproject_pixel<DT>(P, x, y, a0, a1, gin, g0p, hw, g, err);
+    const bool reinit = replay_reprojection<DT>(P, __float_as_uint(hv.y), a0, gin, g0p, hw, g, err);
     const Surf s = make_surf(P, x, y, a0, a1);
     Guide d = derive_guide_shape(P, g, gated(P, reinit, a1));
-    d.Z = __ldcs(zbuf + i);
+    d.Z = hv.x;
     const int kc = (int)fminf(fmaxf(g.k, 0.0f), (float)P.k_max);
     const int n = min(5 + (15 * (P.k_max - kc)) / P.k_max, P.reuse_c);
     const uint4 r = philox4x32_10(make_uint4((uint32_t)i, frame, 0u, 4u), P.rk);
@@ -205,11 +209,11 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
 }  // namespace
 
 cudaError_t launch_pt(int dt, const Params& P, const void* gin, const float4* g0, const float4* g1,
-                      const float4* g0p, float* img, uint32_t frame, float4* vpl, float* pb_src, float* zbuf, int* err,
+                      const float4* g0p, float* img, uint32_t frame, float4* vpl, float* pb_src, float2* hand, int* err,
                       cudaStream_t st) {
     const dim3 grid = grid_for(P);
 #define PG_PT(ONE, RGB) \
-    PG_DISPATCH(dt, (k_pt<D, ONE, RGB><<<grid, kBlock, 0, st>>>(P, gin, g0, g1, g0p, img, frame, vpl, pb_src, zbuf, err)))
+    PG_DISPATCH(dt, (k_pt<D, ONE, RGB><<<grid, kBlock, 0, st>>>(P, gin, g0, g1, g0p, img, frame, vpl, pb_src, hand, err)))
     if (P.spp == 1 && P.rgb) {
         PG_PT(true, true);
     } else if (P.spp == 1) {
@@ -224,7 +228,7 @@ cudaError_t launch_pt(int dt, const Params& P, const void* gin, const float4* g0
 }
 
 cudaError_t launch_train(int dt, const Params& P, const void* gin, void* gout, const float4* g0, const float4* g1,
-                         const float4* g0p, uint32_t frame, const float4* vpl, const float* pb_src, const float* zbuf,
+                         const float4* g0p, uint32_t frame, const float4* vpl, const float* pb_src, const float2* hand,
                          int* err, cudaStream_t st) {
     const int tn = (kTileW + 2 * P.reuse_r) * (kTileH + 2 * P.reuse_r);
     const size_t tile_bytes = (size_t)tn * P.spp * (sizeof(float4) + sizeof(float));
@@ -233,7 +237,7 @@ cudaError_t launch_train(int dt, const Params& P, const void* gin, void* gout, c
         const dim3 grid((unsigned)((P.W + kTileW - 1) / kTileW), (unsigned)((P.H + kTileH - 1) / kTileH));
 #define PG_TRAIN_TILED(ONE) \
     PG_DISPATCH(dt, (k_train<D, ONE, true><<<grid, kBlock, tile_bytes, st>>>(P, gin, gout, g0, g1, g0p, frame, vpl, \
-                                                                             pb_src, zbuf, err)))
+                                                                             pb_src, hand, err)))
         if (P.spp == 1) {
             PG_TRAIN_TILED(true);
         } else {
@@ -242,10 +246,10 @@ cudaError_t launch_train(int dt, const Params& P, const void* gin, void* gout, c
 #undef PG_TRAIN_TILED
     } else if (P.spp == 1) {
         PG_DISPATCH(dt, (k_train<D, true, false><<<grid_for(P), kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, frame,
-                                                                                 vpl, pb_src, zbuf, err)));
+                                                                                 vpl, pb_src, hand, err)));
     } else {
         PG_DISPATCH(dt, (k_train<D, false, false><<<grid_for(P), kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, frame,
-                                                                                  vpl, pb_src, zbuf, err)));
+                                                                                  vpl, pb_src, hand, err)));
     }
     return cudaGetLastError();
 }
