@@ -805,7 +805,7 @@ def run_gpu(args, ws, rank, local):
     __graft_entry__.build()
 
     n_frames = args.warmup + args.steps
-    n_dev = max(n_frames, MSE_RUN_FRAMES)
+    n_dev = n_frames if args.no_mse else max(n_frames, MSE_RUN_FRAMES)
     wl = scenes.workload_pan(1920, 1080, frames=n_dev)
     par, fld, sc = wl["params"], wl["field"], wl["scene"]
     hw = par.width * par.height
@@ -844,7 +844,7 @@ def run_gpu(args, ws, rank, local):
 
     # matched MSE against the FP64 ground truth over frames 30-59 of a
     # separate 60-frame run of each form
-    mse = run_mse_pan(par, sc, fld, g0d, g1d)
+    mse = None if args.no_mse else run_mse_pan(par, sc, fld, g0d, g1d)
 
     e2e_ms, h2d, d2h, link_gbs = run_e2e(par, sc, fld, g0h, g1h, "f16", args.warmup, args.steps, rank)
     del g0h, g1h, g0d, g1d
@@ -913,7 +913,8 @@ def run_gpu(args, ws, rank, local):
                   "value": res["reuse"]["mpix_s"], "ms_per_step": res["reuse"]["ms_per_step"],
                   "hbm_frac": res["reuse"]["gbs"] / peak,
                   "plain_3spp": {"ms_per_step": res["spp3"]["ms_per_step"],
-                                            "image_mse": mse["fp16_3spp"], "reuse_image_mse": mse["fp16_reuse"]},
+                                            "image_mse": mse["fp16_3spp"] if mse else None,
+                                            "reuse_image_mse": mse["fp16_reuse"] if mse else None},
                   "algorithmic_bytes_per_pixel": BYTES_PER_PIXEL["reuse"]},
         "roofline": {"bound": "hbm", "achieved": main["gbs"], "peak": peak, "unit": "GB/s",
                      "frac": main["gbs"] / peak, "peak_kind": peak_kind,
@@ -953,6 +954,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 EM + gradient-step leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the 512x512 Adam-versus-EM comparison")
+    ap.add_argument("--no-mse", action="store_true",
+                    help="skip the matched-MSE leg (its 60 frames of G-buffers on the device): for small profiling runs")
     ap.add_argument("--orbit-step", default=None, metavar="WxH",
                     help="run four steps of the orbit workload at WxH and exit (the program of its ncu captures)")
     ap.add_argument("--no-temporal", action="store_true",

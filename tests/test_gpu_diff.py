@@ -52,7 +52,7 @@ def test_adam_versus_em_comparison_matches_oracle():
     sys.path.insert(0, ROOT)
     import bench
     W, spp, steps, lr, ev = 16, 16, 10, 1e-2, 4
-    got = bench.run_diff(W, W, spp=spp, steps=steps, lr=lr, eval_frames=ev, ref_spp=64)
+    got = bench.run_diff(W, W, spp=spp, steps=steps, lr=lr, eval_frames=ev)
     ref = _oracle_scores(W, spp, steps, lr, ev)
     for k in ("initial", "em", "adam"):
         assert abs(got[k]["second_moment"] - ref[k]) <= 5e-3 * ref[k], (k, got[k], ref[k])

@@ -271,3 +271,31 @@ def test_stochastic_rounding_is_unbiased_on_the_gpu(dtype):
     assert np.max(err) < 5.0 / (2 * np.sqrt(n)) + 0.02, np.max(err)
     rn_err = np.abs(_round(exact, dtype) - exact)[moved] / ulp[moved]
     assert rn_err.mean() > 5 * err.mean()
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_16_bit_store_rounds_to_nearest_and_saturates(dtype):
+    """The 16-bit store of Gamma, bit for bit: round to nearest, FP16
+    saturating at +-65504 (also for values that would round to infinity) and
+    keeping its subnormals, BF16 unclamped. With a zero mean the stored central
+    moments are the given second moments exactly, so every field of the record
+    is a given binary32 value rounded once."""
+    import torch
+    W, H = 64, 8
+    hw = W * H
+    rng = np.random.default_rng(5)
+    mag = np.exp(rng.uniform(np.log(1e-9), np.log(3e5), (hw, 8)))
+    vals = (mag * rng.choice([-1.0, 1.0], (hw, 8))).astype(np.float32)
+    vals[:, 0:2] = 0.0                                     # the mean: central = raw second moments
+    vals[:8, 7] = np.float32([65504, 65519.9, 65520, 1e6, -65520, -1e9, 6e-8, 3e-5])
+    par = scenes.Params(W, H)
+    gp = guide(par, dtype)
+    set_gamma_rows(gp, vals)
+    rec = host(gp.pg_get_gamma())
+    gp.close()
+    t = torch.from_numpy(vals.astype(np.float32))
+    if dtype == "f16":
+        ref = t.clamp(-65504.0, 65504.0).to(torch.float16)
+    else:
+        ref = t.to(torch.bfloat16)
+    assert np.array_equal(rec, ref.contiguous().view(torch.uint8).reshape(-1).numpy())
