@@ -16,10 +16,17 @@ namespace {
 //   dp/dSigma = pi (g/2 (Sigma^-1 d d^T Sigma^-1 - Sigma^-1) - p_b dZ/dSigma)
 // for theta = (mu_x, mu_y, s_xx, s_yy, s_xy, pi), s_xy a single parameter.
 // ---------------------------------------------------------------------------
-// Four blocks of 256 per SM (64 registers, no spills): 0.99 ms for the
-// 3840x2160 orbit step at 4 draws, against 1.21 ms at the register count
-// the compiler picks unbounded (94, two blocks) and 1.12 ms at five blocks
-// (48 registers, spilling).
+// The sums over the draws are factored so that nothing of Z's derivative is
+// live in the loop: with c = -f^2/p^3 and cg = c p_g,
+//   dl/dmu    ~ pi (sum cg Sigma^-1 d - dZ/dmu sum c p_b),
+//   dl/dSigma ~ pi (1/2 (sum cg (Sigma^-1 d)(Sigma^-1 d)^T - Sigma^-1 sum cg) - dZ/dSigma sum c p_b),
+//   dl/dpi    ~ sum cg - Z sum c p_b,
+// eight binary32 sums (the loss, five of cg times a monomial of Sigma^-1 d,
+// sum cg and sum c p_b); dZ/dtheta is taken once, after the loop.
+// Four blocks of 256 per SM (64 registers, 8 bytes spilled): 0.91 ms for the
+// 3840x2160 orbit step at 4 draws, against 1.21 ms at the register count the
+// compiler picks unbounded (two blocks) and 1.12 ms at five blocks (48
+// registers, more spills).
 template <int DT, bool THETA>
 __global__ void __launch_bounds__(kBlock, 4) k_grad(const Params P, const void* __restrict__ gam,
                                                  const float* __restrict__ theta, const float4* __restrict__ g0,
@@ -40,32 +47,45 @@ __global__ void __launch_bounds__(kBlock, 4) k_grad(const Params P, const void* 
     }
     const Surf s = make_surf(P, x, y, a0, a1);
     const Guide d = derive_guide(P, g, gated(P, false, a1));
-    float dz[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     const bool guided = d.pi_eff > 0.0f;
-    if (guided) rect_mass_grad(d, dz);
-    const float det = fmaf(d.sxx, d.syy, -d.sxy * d.sxy), idet = fdiv(1.0f, det);
+    // Sigma^-1 = [[qxx, -qxy], [-qxy, qyy]]
+    const float idet = fdiv(1.0f, fmaf(d.sxx, d.syy, -d.sxy * d.sxy));
+    const float qxx = d.syy * idet, qyy = d.sxx * idet, qxy = d.sxy * idet;
     // plain binary32 sums: at most a few hundred draws of one pixel, whose
     // rounding (~n 2^-24 of the summed magnitudes) is far inside the
     // adjoint's 1e-3 parity bound; compensation cost ~5% of the kernel
-    float l = 0.0f, gs[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float l = 0.0f, ax = 0.0f, ay = 0.0f, axx = 0.0f, ayy = 0.0f, axy = 0.0f, sg = 0.0f, sb = 0.0f;
     for (int si = 0; si < n; ++si) {
         const Smp o = draw_sample(P, d, s, (uint32_t)i, frame, (uint32_t)si, 2u);
         if ((o.strat & ST_INVALID) || o.fcos == 0.0f || !(o.pmix > 0.0f)) continue;
-        const float ip = fdiv(1.0f, o.pmix), f2 = o.fcos * o.fcos;
-        l += f2 * ip * ip;
+        const float ip = fdiv(1.0f, o.pmix), f2ip2 = o.fcos * o.fcos * ip * ip;
+        l += f2ip2;
         if (!guided) continue;
         const float dx = o.ux - d.mx, dy = o.uy - d.my;
-        const float ix = (d.syy * dx - d.sxy * dy) * idet, iy = (d.sxx * dy - d.sxy * dx) * idet;
-        const float c = -f2 * ip * ip * ip, pe = d.pi_eff;
-        gs[0] += (c * pe * (o.pg * ix - o.pb * dz[0]));
-        gs[1] += (c * pe * (o.pg * iy - o.pb * dz[1]));
-        gs[2] += (c * pe * (o.pg * 0.5f * (ix * ix - d.syy * idet) - o.pb * dz[2]));
-        gs[3] += (c * pe * (o.pg * 0.5f * (iy * iy - d.sxx * idet) - o.pb * dz[3]));
-        gs[4] += (c * pe * (o.pg * (ix * iy + d.sxy * idet) - o.pb * dz[4]));
-        gs[5] += (c * (o.pg - d.Z * o.pb));
+        const float ix = fmaf(qxx, dx, -qxy * dy), iy = fmaf(qyy, dy, -qxy * dx);
+        const float c = -f2ip2 * ip, cg = c * o.pg;
+        ax = fmaf(cg, ix, ax);
+        ay = fmaf(cg, iy, ay);
+        axx = fmaf(cg * ix, ix, axx);
+        ayy = fmaf(cg * iy, iy, ayy);
+        axy = fmaf(cg * ix, iy, axy);
+        sg += cg;
+        sb = fmaf(c, o.pb, sb);
     }
     const float in = 1.0f / (float)n;
     loss[i] = l * in;
+    float gs[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (guided) {
+        float dz[5];
+        rect_mass_grad(d, dz);
+        const float pe = d.pi_eff;
+        gs[0] = pe * fmaf(-sb, dz[0], ax);
+        gs[1] = pe * fmaf(-sb, dz[1], ay);
+        gs[2] = pe * fmaf(-sb, dz[2], 0.5f * fmaf(-qxx, sg, axx));
+        gs[3] = pe * fmaf(-sb, dz[3], 0.5f * fmaf(-qyy, sg, ayy));
+        gs[4] = pe * fmaf(-sb, dz[4], fmaf(qxy, sg, axy));
+        gs[5] = fmaf(-d.Z, sb, sg);
+    }
 #pragma unroll
     for (int k = 0; k < 6; ++k) grad[k * hw + i] = gs[k] * in;
 }
