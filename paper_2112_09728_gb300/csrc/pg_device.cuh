@@ -115,6 +115,17 @@ __device__ __forceinline__ float unit24_open0(uint32_t w) {
 // latter's slow path is then taken only for extreme operands).
 __device__ __forceinline__ float fdiv(float x, float y) { return y > 1e-30f ? __fdividef(x, y) : __fdiv_rn(x, y); }
 
+// Pairs of binary32 values: sm_100's paired FMA, multiply and add issue once
+// for both halves, each half rounded as the scalar operation would round it,
+// so code written on pairs gives the scalar code's bits in half the issue
+// slots of its arithmetic.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
 // 2^x by the hardware approximation (relative error below 2^-22 over the
 // normal range; results below the smallest normal flush to zero).
 __device__ __forceinline__ float exp2_approx(float x) {
@@ -522,6 +533,39 @@ __device__ __forceinline__ float normal_tail(float h) {
     return 0.5f * t * exp2_approx(fmaf(-x, x, q) * 1.44269504088896341f);
 }
 
+// normal_tail of two arguments at once: the same operations on each half.
+__device__ __forceinline__ float2 normal_tail2(float2 h) {
+    const float2 x = mul2(h, dup2(0.70710678118654752f));
+    const float2 den = fma2(dup2(0.5f), x, dup2(1.0f));
+    const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+    const float2 s = add2(t, dup2(-0.66f));
+    float2 q = dup2(1.351362865e-02f);
+    q = fma2(q, s, dup2(1.648487823e-01f));
+    q = fma2(q, s, dup2(-1.294304248e-01f));
+    q = fma2(q, s, dup2(-1.525244650e-01f));
+    q = fma2(q, s, dup2(2.444149027e-01f));
+    q = fma2(q, s, dup2(7.020706726e-02f));
+    q = fma2(q, s, dup2(-4.014188533e-01f));
+    q = fma2(q, s, dup2(-2.941247197e-03f));
+    q = fma2(q, s, dup2(1.375446506e+00f));
+    q = fma2(q, s, dup2(-4.533098012e-01f));
+    const float2 e = mul2(fma2(neg2(x), x, q), dup2(1.44269504088896341f));
+    const float2 v = mul2(mul2(dup2(0.5f), t), make_float2(exp2_approx(e.x), exp2_approx(e.y)));
+    return make_float2(h.x < 5.66f ? v.x : 0.0f, h.y < 5.66f ? v.y : 0.0f);
+}
+
+// sin_small of two arguments at once.
+__device__ __forceinline__ float2 sin_small2(float2 t) {
+    const float2 t2 = mul2(t, t);
+    float2 p = dup2(1.6059043836821613e-10f);
+    p = fma2(p, t2, dup2(-2.5052108385441720e-8f));
+    p = fma2(p, t2, dup2(2.7557319223985891e-6f));
+    p = fma2(p, t2, dup2(-1.9841269841269841e-4f));
+    p = fma2(p, t2, dup2(8.3333333333333333e-3f));
+    p = fma2(p, t2, dup2(-1.6666666666666667e-1f));
+    return fma2(mul2(t, t2), p, t);
+}
+
 // Z by four corners of the bivariate normal cdf in the Drezner-Wesolowsky form
 //   Phi_2(h,k;rho) = Phi(h)Phi(k) + 1/(2 pi) int_0^asin(rho) exp(-(h^2+k^2-2hk sin t)/(2 cos^2 t)) dt,
 // so Z = (Phi(h1)-Phi(h0)) (Phi(k1)-Phi(k0)) + signed sum of the four corner
@@ -533,9 +577,10 @@ __device__ __forceinline__ float normal_tail(float h) {
 __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, float isx, float isy, float rho) {
     const float h0 = -mx * isx, h1 = (1.0f - mx) * isx;
     const float k0 = -my * isy, k1 = (1.0f - my) * isy;
-    const float dpx = 1.0f - normal_tail(-h0) - normal_tail(h1);
-    const float dpy = 1.0f - normal_tail(-k0) - normal_tail(k1);
-    float z = dpx * dpy;
+    // the tails of both axes in pairs: (T(-h0), T(-k0)) and (T(h1), T(k1))
+    const float2 ta = normal_tail2(make_float2(-h0, -k0)), tb = normal_tail2(make_float2(h1, k1));
+    const float2 dp = sub2(sub2(dup2(1.0f), ta), tb);
+    float z = dp.x * dp.y;
     const float h0s = h0 * h0, h1s = h1 * h1, k0s = k0 * k0, k1s = k1 * k1;
     // a corner contributes below e^-18 when its exponent bound exceeds 18:
     // (h^2 + k^2)/2 if h k rho <= 0 (the cross term only adds), else max(h^2, k^2)/2
@@ -553,17 +598,25 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
         const float a11 = (h1s + k1s) * l2, b11 = 2.0f * h1 * k1 * l2;
         const float a10 = (h1s + k0s) * l2, b10 = 2.0f * h1 * k0 * l2;
         const float a01 = (h0s + k1s) * l2, b01 = 2.0f * h0 * k1 * l2;
+        auto corner = [](float b, float a, float2 s, float2 q) {
+            const float2 e = mul2(fma2(dup2(b), s, dup2(-a)), q);
+            return make_float2(exp2_approx(e.x), exp2_approx(e.y));
+        };
         float acc = 0.0f;
+        // two nodes at a time, each half of a pair one node
 #pragma unroll
-        for (int i = 0; i < kGLNodes; ++i) {
-            const float s = sin_small(fmaf(half, P.gl_x[i], half));
-            const float q = __fdividef(1.0f, fmaf(-s, s, 1.0f));     // 1 / cos^2 t, cos^2 t >= 0.19
-            float v = 0.0f;
-            if (c00) v += exp2_approx(fmaf(b00, s, -a00) * q);
-            if (c11) v += exp2_approx(fmaf(b11, s, -a11) * q);
-            if (c10) v -= exp2_approx(fmaf(b10, s, -a10) * q);
-            if (c01) v -= exp2_approx(fmaf(b01, s, -a01) * q);
-            acc = fmaf(P.gl_w[i], v, acc);
+        for (int i = 0; i < kGLNodes; i += 2) {
+            const float2 hh = dup2(half);
+            const float2 s = sin_small2(fma2(hh, make_float2(P.gl_x[i], P.gl_x[i + 1]), hh));
+            const float2 om = fma2(neg2(s), s, dup2(1.0f));
+            const float2 q = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));  // 1 / cos^2 t >= 1
+            float2 v = dup2(0.0f);
+            if (c00) v = add2(v, corner(b00, a00, s, q));
+            if (c11) v = add2(v, corner(b11, a11, s, q));
+            if (c10) v = sub2(v, corner(b10, a10, s, q));
+            if (c01) v = sub2(v, corner(b01, a01, s, q));
+            acc = fmaf(P.gl_w[i], v.x, acc);
+            acc = fmaf(P.gl_w[i + 1], v.y, acc);
         }
         z = fmaf(acc, half * kInv2Pi, z);
     }
@@ -985,8 +1038,22 @@ struct Kahan {
     __device__ __forceinline__ void set(float v) { s = v; }
 };
 
+// Two Kahan sums advanced together, each half as Kahan::add.
+struct Kahan2 {
+    float2 s = {0.0f, 0.0f}, c = {0.0f, 0.0f};
+    __device__ __forceinline__ void add(float2 v) {
+        const float2 y = sub2(v, c);
+        const float2 t = add2(s, y);
+        c = sub2(sub2(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ void set(float2 v) { s = v; }
+};
+
 struct Stats {
-    Kahan a, b, s1x, s1y, s2xx, s2yy, s2xy;
+    // (a, b), (S1x, S1y), (S2xx, S2yy) in pairs and S2xy alone
+    Kahan2 ab, s1, s2;
+    Kahan s2xy;
     bool empty = true;
     __device__ __forceinline__ void add_train(const Guide& d, const Gam& g, const Smp& o) {
         if (o.strat != ST_BRDF || !(o.pb > 0.0f)) return;
@@ -1023,25 +1090,22 @@ struct Stats {
     }
     __device__ __forceinline__ void add(const Gam& g, float w, float gam, float ux, float uy) {
         const float wg = w * gam;
-        const float dx = ux - g.ex, dy = uy - g.ey;
+        const float2 d = sub2(make_float2(ux, uy), make_float2(g.ex, g.ey));
+        const float2 wd = mul2(dup2(wg), d);        // (wg dx, wg dy)
+        const float2 wdd = mul2(wd, d);             // (wg dx dx, wg dy dy)
+        const float wxy = wd.x * d.y;               // wg dx dy
         if (empty) {
-            a.set(wg);
-            b.set(w);
-            s1x.set(wg * dx);
-            s1y.set(wg * dy);
-            s2xx.set(wg * dx * dx);
-            s2yy.set(wg * dy * dy);
-            s2xy.set(wg * dx * dy);
+            ab.set(make_float2(wg, w));
+            s1.set(wd);
+            s2.set(wdd);
+            s2xy.set(wxy);
             empty = false;
             return;
         }
-        a.add(wg);
-        b.add(w);
-        s1x.add(wg * dx);
-        s1y.add(wg * dy);
-        s2xx.add(wg * dx * dx);
-        s2yy.add(wg * dy * dy);
-        s2xy.add(wg * dx * dy);
+        ab.add(make_float2(wg, w));
+        s1.add(wd);
+        s2.add(wdd);
+        s2xy.add(wxy);
     }
 };
 
@@ -1057,7 +1121,7 @@ struct Stats {
 // moments in binary32. A frame with b = 0 changes nothing.
 __device__ __forceinline__ void m_step(const Params& P, Gam& g, const Stats& st) {
     const float k = fmaxf(g.k, 0.0f);
-    const float a = st.a.s, b = st.b.s;
+    const float a = st.ab.s.x, b = st.ab.s.y;
     g.k = k;
     if (!(b > 0.0f)) return;
     const float eta = __fdividef(1.0f, fminf(k, (float)P.k_max) + 2.0f);   // an integer in [2, k_max + 2]
@@ -1070,18 +1134,28 @@ __device__ __forceinline__ void m_step(const Params& P, Gam& g, const Stats& st)
         // lambda delta = eta S1 / A and lambda M2 = eta S2 / A: bounded ratios,
         // by one hardware reciprocal of A while A is normal (2 ulp, as fdiv's
         // fast path), by correctly rounded divisions for a subnormal A
-        const bool fast = A > 1e-30f;
-        const float rA = __fdividef(1.0f, fast ? A : 1.0f);
-        auto byA = [&](float v) { return fast ? v * rA : __fdiv_rn(v, A); };
-        const float lam = byA(eta * a), l1 = 1.0f - lam;
-        const float ldx = byA(eta * st.s1x.s), ldy = byA(eta * st.s1y.s);
-        const float lmxx = byA(eta * st.s2xx.s), lmyy = byA(eta * st.s2yy.s);
-        const float lmxy = byA(eta * st.s2xy.s);
-        g.sxx = fmaf(l1, g.sxx, fmaf(-ldx, ldx, lmxx));
-        g.syy = fmaf(l1, g.syy, fmaf(-ldy, ldy, lmyy));
-        g.sxy = fmaf(l1, g.sxy, fmaf(-ldx, ldy, lmxy));
-        g.ex += ldx;
-        g.ey += ldy;
+        float lam, lmxy;
+        float2 ld, lm;          // (lambda dx, lambda dy), (lambda M2xx, lambda M2yy)
+        if (A > 1e-30f) {
+            const float rA = __fdividef(1.0f, A);
+            lam = eta * a * rA;
+            ld = mul2(mul2(dup2(eta), st.s1.s), dup2(rA));
+            lm = mul2(mul2(dup2(eta), st.s2.s), dup2(rA));
+            lmxy = eta * st.s2xy.s * rA;
+        } else {
+            lam = __fdiv_rn(eta * a, A);
+            ld = make_float2(__fdiv_rn(eta * st.s1.s.x, A), __fdiv_rn(eta * st.s1.s.y, A));
+            lm = make_float2(__fdiv_rn(eta * st.s2.s.x, A), __fdiv_rn(eta * st.s2.s.y, A));
+            lmxy = __fdiv_rn(eta * st.s2xy.s, A);
+        }
+        const float l1 = 1.0f - lam;
+        const float2 sd = fma2(dup2(l1), make_float2(g.sxx, g.syy), fma2(neg2(ld), ld, lm));
+        g.sxx = sd.x;
+        g.syy = sd.y;
+        g.sxy = fmaf(l1, g.sxy, fmaf(-ld.x, ld.y, lmxy));
+        const float2 e = add2(make_float2(g.ex, g.ey), ld);
+        g.ex = e.x;
+        g.ey = e.y;
         raw_from_central(g);
     }
     g.pi = fminf(fmaxf(fdiv(A, B), P.pi_min), P.pi_max);
