@@ -61,6 +61,9 @@ struct Params {
     int n_lobes, mask_kind;
     float lobe_dir[8][3], lobe_kappa[8], lobe_scale[8];  // scale = amp * vMF normaliser
     float lobe_e2[8];                                     // -kappa log2(e) / 2: exponent per |w - d|^2 in base 2
+    // the same lobes in pairs (2i, 2i+1) for paired arithmetic: negated
+    // direction components and exponent factors (zero beyond n_lobes)
+    float2 lobe_pnx[4], lobe_pny[4], lobe_pnz[4], lobe_pe2[4];
     float field_const, mask[3];
     // coloured field: per-lobe scale of each channel and the constant's
     // channels (lobe_scale and field_const then hold the luminance)
@@ -134,6 +137,15 @@ __device__ __forceinline__ float exp2_approx(float x) {
     return y;
 }
 
+// Square root by the hardware approximation (sqrt.approx.f32), for the
+// per-sample geometry where a correctly rounded root buys nothing: a few ulp
+// of a direction component are far below the parity tolerances.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // sin and cos of 2 pi x for x in [0, 1): shifted by half a turn into [-pi, pi),
 // where the hardware approximation holds its 2^-21.4 absolute accuracy.
 __device__ __forceinline__ void sincos_turn(float x, float* s, float* c) {
@@ -156,7 +168,7 @@ struct Basis {
 };
 __device__ __forceinline__ Basis make_basis(float3 n) {
     const float sg = copysignf(1.0f, n.z);
-    const float a = -1.0f / (sg + n.z);
+    const float a = __fdividef(-1.0f, sg + n.z);   // sg + n.z in [1, 2] for a unit normal
     const float c = n.x * n.y * a;
     Basis f;
     f.n = n;
@@ -181,23 +193,16 @@ __device__ __forceinline__ float3 to_local(const Basis& f, float3 w) {
 __device__ __forceinline__ float3 square_to_hemi(float u, float v) {
     const float a = 2.0f * u - 1.0f, b = 2.0f * v - 1.0f;
     if (a == 0.0f && b == 0.0f) return make_float3(0.0f, 0.0f, 1.0f);
-    float r, m, s, c, dx, dy;
-    if (fabsf(a) > fabsf(b)) {
-        r = a;
-        m = fminf(u, 1.0f - u);
-        __sincosf(0.78539816339744831f * __fdividef(b, a), &s, &c);
-        dx = r * c;
-        dy = r * s;
-    } else {
-        r = b;
-        m = fminf(v, 1.0f - v);
-        __sincosf(0.78539816339744831f * __fdividef(a, b), &s, &c);
-        dx = r * s;
-        dy = r * c;
-    }
+    // either dominant axis by the same instructions (no divergent sincos sites)
+    const bool xd = fabsf(a) > fabsf(b);
+    const float r = xd ? a : b;
+    const float m = xd ? fminf(u, 1.0f - u) : fminf(v, 1.0f - v);
+    float s, c;
+    __sincosf(0.78539816339744831f * __fdividef(xd ? b : a, r), &s, &c);
     const float z = 4.0f * m * (1.0f - m);
-    const float lift = sqrtf(1.0f + z);
-    return make_float3(dx * lift, dy * lift, z);
+    const float lift = sqrt_approx(1.0f + z);
+    const float2 d = mul2(mul2(dup2(r), xd ? make_float2(c, s) : make_float2(s, c)), dup2(lift));
+    return make_float3(d.x, d.y, z);
 }
 
 // (4/pi) atan(t) for t in [-1, 1]: t P(t^2) with P of degree 7, this
@@ -223,7 +228,7 @@ __device__ __forceinline__ float2 hemi_to_square(float3 w) {
     const float z = fmaxf(w.z, 0.0f);
     const float inv = rsqrtf(1.0f + z);
     const float dx = w.x * inv, dy = w.y * inv;
-    const float r = sqrtf(dx * dx + dy * dy);
+    const float r = sqrt_approx(dx * dx + dy * dy);
     if (r < 1e-30f) return make_float2(0.5f, 0.5f);   // the pole (to within 1e-30)
     const bool xdom = fabsf(dx) >= fabsf(dy);
     const float lead = xdom ? dx : dy, other = xdom ? dy : dx;
@@ -592,12 +597,18 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
     const bool c01 = live(h0, k1, h0s, k1s), c11 = live(h1, k1, h1s, k1s);
     if (rho != 0.0f && (c00 || c10 || c01 || c11)) {
         const float asr = asinf(rho), half = 0.5f * asr;
-        // exponent of corner (h, k) in base 2: (2hk s - h^2 - k^2) log2(e) / (2 cos^2 t)
+        // exponent of corner (h, k) in base 2: (2hk s - h^2 - k^2) log2(e) / (2 cos^2 t);
+        // a skipped corner gets a = +inf, so that its terms are exactly 0
         const float l2 = 0.72134752044448170f;                  // log2(e) / 2
-        const float a00 = (h0s + k0s) * l2, b00 = 2.0f * h0 * k0 * l2;
-        const float a11 = (h1s + k1s) * l2, b11 = 2.0f * h1 * k1 * l2;
-        const float a10 = (h1s + k0s) * l2, b10 = 2.0f * h1 * k0 * l2;
-        const float a01 = (h0s + k1s) * l2, b01 = 2.0f * h0 * k1 * l2;
+        const float inf = __int_as_float(0x7f800000);
+        const float a00 = c00 ? (h0s + k0s) * l2 : inf, b00 = 2.0f * h0 * k0 * l2;
+        const float a11 = c11 ? (h1s + k1s) * l2 : inf, b11 = 2.0f * h1 * k1 * l2;
+        const float a10 = c10 ? (h1s + k0s) * l2 : inf, b10 = 2.0f * h1 * k0 * l2;
+        const float a01 = c01 ? (h0s + k1s) * l2 : inf, b01 = 2.0f * h0 * k1 * l2;
+        // a corner no lane of the warp needs is left out by the whole warp
+        const unsigned act = __activemask();
+        const bool w00 = __any_sync(act, c00), w11 = __any_sync(act, c11);
+        const bool w10 = __any_sync(act, c10), w01 = __any_sync(act, c01);
         auto corner = [](float b, float a, float2 s, float2 q) {
             const float2 e = mul2(fma2(dup2(b), s, dup2(-a)), q);
             return make_float2(exp2_approx(e.x), exp2_approx(e.y));
@@ -611,10 +622,10 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
             const float2 om = fma2(neg2(s), s, dup2(1.0f));
             const float2 q = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));  // 1 / cos^2 t >= 1
             float2 v = dup2(0.0f);
-            if (c00) v = add2(v, corner(b00, a00, s, q));
-            if (c11) v = add2(v, corner(b11, a11, s, q));
-            if (c10) v = sub2(v, corner(b10, a10, s, q));
-            if (c01) v = sub2(v, corner(b01, a01, s, q));
+            if (w00) v = add2(v, corner(b00, a00, s, q));
+            if (w11) v = add2(v, corner(b11, a11, s, q));
+            if (w10) v = sub2(v, corner(b10, a10, s, q));
+            if (w01) v = sub2(v, corner(b01, a01, s, q));
             acc = fmaf(P.gl_w[i], v.x, acc);
             acc = fmaf(P.gl_w[i + 1], v.y, acc);
         }
@@ -692,7 +703,7 @@ __device__ __forceinline__ float dielectric_fresnel(float ci) {
 }
 
 __device__ __forceinline__ float smith_g1(float a2, float c) {
-    return __fdividef(2.0f * c, c + sqrtf(fmaf(1.0f - a2, c * c, a2)));
+    return __fdividef(2.0f * c, c + sqrt_approx(fmaf(1.0f - a2, c * c, a2)));
 }
 
 // GLASS = false compiles the transparent material out (its code is then
@@ -736,7 +747,7 @@ __device__ __forceinline__ Surf make_surf(const Params& P, int x, int y, float4 
 __device__ __forceinline__ void ggx_eval(const Surf& s, float wiz, float ct, float st2, float oh, float& fcos,
                                          float& pb, float f0) {
     const float t = fmaf(s.a2, ct * ct, st2);
-    const float e = wiz + sqrtf(fmaf(1.0f - s.a2, wiz * wiz, s.a2));
+    const float e = wiz + sqrt_approx(fmaf(1.0f - s.a2, wiz * wiz, s.a2));
     const float den = kPi * t * t * e * oh;
     const float r = den > 1e-30f ? __fdividef(1.0f, den) : __fdiv_rn(1.0f, den);
     const float a2r = s.a2 * r;
@@ -807,13 +818,13 @@ __device__ __forceinline__ bool glass_sample(const Surf& s, float x1, float3& wi
 __device__ __forceinline__ bool brdf_sample_sc(const Surf& s, float x1, float sn, float cs, float3& wi, float& hct,
                                                float& hst2, float& hoh) {
     if (s.mat == MAT_LAMBERT) {
-        const float r = sqrtf(x1);
-        wi = make_float3(r * cs, r * sn, sqrtf(1.0f - x1));
+        const float r = sqrt_approx(x1);
+        wi = make_float3(r * cs, r * sn, sqrt_approx(1.0f - x1));
         return true;
     }
     const float id = __fdividef(1.0f, (1.0f - x1) + s.a2 * x1);
     const float st2 = s.a2 * x1 * id;
-    const float ct = sqrtf((1.0f - x1) * id), st = sqrtf(st2);
+    const float ct = sqrt_approx((1.0f - x1) * id), st = sqrt_approx(st2);
     const float3 h = make_float3(st * cs, st * sn, ct);
     const float oh = dot3(s.wo, h);
     wi = make_float3(2.0f * oh * h.x - s.wo.x, 2.0f * oh * h.y - s.wo.y, 2.0f * oh * h.z - s.wo.z);
@@ -828,27 +839,69 @@ __device__ __forceinline__ bool brdf_sample_sc(const Surf& s, float x1, float sn
 // Each lobe is amp * C_k exp(-k |w - d|^2 / 2) (= amp * C_k exp(k (d.w - 1))
 // for unit vectors, in a form that keeps its precision near the peak).
 // ---------------------------------------------------------------------------
+// sqrt(2) sin(pi x / 2) for each half of x in [0, 1/2]: x P(x^2) with P of
+// degree 3, this library's own fit (fit_mask_sine.py; relative error 3e-9,
+// 1.3e-7 in binary32). Its square is 1 - cos(pi x) to 3.2e-7 relative.
+__device__ __forceinline__ float2 sqrt2_sin_half_pi(float2 x) {
+    const float2 x2 = mul2(x, x);
+    float2 p = dup2(-6.507568864e-03f);
+    p = fma2(p, x2, dup2(1.126845176e-01f));
+    p = fma2(p, x2, dup2(-9.135302789e-01f));
+    p = fma2(p, x2, dup2(2.221441462e+00f));
+    return mul2(p, x);
+}
+
+// The occlusion mask m = (1 + sin(pi A) cos(pi B)) / 2, A and B in
+// half-turns. Both phases are reduced exactly to [-1, 1] (A - 2 rint(A/2) is
+// representable), then written through the distance e of A to the nearest
+// half-integer and the distance d of B to the nearest integer:
+// |sin(pi A)| = 1 - vs, |cos(pi B)| = 1 - vc with vs = 1 - cos(pi e) and
+// vc = 1 - cos(pi d), each from the fitted sine without cancellation. Where
+// the product is negative m = (vs + vc - vs vc) / 2, so m keeps its relative
+// precision as it approaches 0; elsewhere m = (1 + (1 - vs)(1 - vc)) / 2.
+__device__ __forceinline__ float occlusion_mask(float A, float B) {
+    const float2 ab = make_float2(A, B);
+    const float2 h = mul2(ab, dup2(0.5f));
+    const float2 r = fma2(dup2(-2.0f), make_float2(rintf(h.x), rintf(h.y)), ab);
+    const float ar = fabsf(r.x), br = fabsf(r.y);
+    const float e = fabsf(0.5f - ar);      // exact for ar >= 1/4 (Sterbenz)
+    const float d = fminf(br, 1.0f - br);  // exact
+    const float2 q = sqrt2_sin_half_pi(make_float2(e, d));
+    const float2 v = mul2(q, q);           // (vs, vc)
+    const bool neg = (r.x < 0.0f) != (br > 0.5f);
+    return neg ? 0.5f * fmaf(-v.x, v.y, v.x + v.y) : 0.5f * fmaf(1.0f - v.x, 1.0f - v.y, 1.0f);
+}
+
 // Returns the radiance's luminance (the field itself when monochrome); with
-// RGB, *rgb receives its three channels (coloured fields).
+// RGB, *rgb receives its three channels (coloured fields). The lobes go in
+// pairs (each half the scalar operations of one lobe), summed in lobe order.
 template <bool RGB = false>
 __device__ __forceinline__ float radiance(const Params& P, float3 pos, float3 w, float3* rgb = nullptr) {
     float s = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
+    const float2 wx = dup2(w.x), wy = dup2(w.y), wz = dup2(w.z);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int jp = 0; jp < 4; ++jp) {
+        const int j = 2 * jp;
         if (j < P.n_lobes) {
-            const float dx = w.x - P.lobe_dir[j][0], dy = w.y - P.lobe_dir[j][1], dz = w.z - P.lobe_dir[j][2];
-            const float e = exp2_approx(P.lobe_e2[j] * fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            s = fmaf(P.lobe_scale[j], e, s);
+            const float2 dx = add2(wx, P.lobe_pnx[jp]), dy = add2(wy, P.lobe_pny[jp]), dz = add2(wz, P.lobe_pnz[jp]);
+            const float2 q = mul2(P.lobe_pe2[jp], fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))));
+            const float e0 = exp2_approx(q.x), e1 = exp2_approx(q.y);
+            // a lobe beyond n_lobes has scale 0 and exponent 0: it adds exactly 0
+            s = fmaf(P.lobe_scale[j], e0, s);
+            s = fmaf(P.lobe_scale[j + 1], e1, s);
             if (RGB) {
-                sr = fmaf(P.lobe_rgb[j][0], e, sr);
-                sg = fmaf(P.lobe_rgb[j][1], e, sg);
-                sb = fmaf(P.lobe_rgb[j][2], e, sb);
+                sr = fmaf(P.lobe_rgb[j][0], e0, sr);
+                sg = fmaf(P.lobe_rgb[j][1], e0, sg);
+                sb = fmaf(P.lobe_rgb[j][2], e0, sb);
+                sr = fmaf(P.lobe_rgb[j + 1][0], e1, sr);
+                sg = fmaf(P.lobe_rgb[j + 1][1], e1, sg);
+                sb = fmaf(P.lobe_rgb[j + 1][2], e1, sb);
             }
         }
     }
     if (P.mask_kind == 1) {
-        const float m = 0.5f + 0.5f * sinpif(2.0f * (P.mask[0] * pos.x + P.mask[2] * w.x)) *
-                                   cospif(2.0f * (P.mask[1] * pos.y + P.mask[2] * w.y));
+        const float m = occlusion_mask(2.0f * (P.mask[0] * pos.x + P.mask[2] * w.x),
+                                       2.0f * (P.mask[1] * pos.y + P.mask[2] * w.y));
         s *= m;
         if (RGB) {
             sr *= m;
@@ -951,7 +1004,7 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
         o.strat = ST_DELTA;
         valid = glass_sample(s, x1, o.wl);
     } else if (zeta < d.pi_eff) {
-        const float rr = sqrtf(-2.0f * __logf(unit24_open0(r0.y)));
+        const float rr = sqrt_approx(-2.0f * __logf(unit24_open0(r0.y)));
         const float z1 = rr * cs, z2 = rr * sn;
         o.ux = fmaf(d.l11, z1, d.mx);
         o.uy = fmaf(d.l22, z2, fmaf(d.l21, z1, d.my));
@@ -991,40 +1044,63 @@ __device__ __forceinline__ Smp draw_sample(const Params& P, const Guide& d, cons
 //   dPhi2/drho = exp(-(h^2 - 2 rho h k + k^2)/(2(1-rho^2))) / (2 pi sqrt(1-rho^2)),
 // chained through h = (a - mu_x)/s_x, k = (b - mu_y)/s_y, rho = s_xy/(s_x s_y).
 // ---------------------------------------------------------------------------
-// Phi(x) from the fitted upper tail (normal_tail): within 2e-7 absolute.
-__device__ __forceinline__ float normal_cdf(float x) {
-    const float t = normal_tail(fabsf(x));
-    return x >= 0.0f ? 1.0f - t : t;
+// Phi(x) of both halves from the fitted upper tail (normal_tail2): within
+// 2e-7 absolute.
+__device__ __forceinline__ float2 normal_cdf2(float2 x) {
+    const float2 t = normal_tail2(make_float2(fabsf(x.x), fabsf(x.y)));
+    return make_float2(x.x >= 0.0f ? 1.0f - t.x : t.x, x.y >= 0.0f ? 1.0f - t.y : t.y);
 }
 
+// exp(x) of both halves as 2^(x log2 e) by the hardware approximation.
+__device__ __forceinline__ float2 exp2x(float2 x) {
+    const float2 e = mul2(x, dup2(1.44269504088896341f));
+    return make_float2(exp2_approx(e.x), exp2_approx(e.y));
+}
+
+// The two axes of each corner go in pairs: (h, k), (dPhi2/dh, dPhi2/dk) and
+// the (s_xx, s_yy) and (mu_x, mu_y) components of the gradient.
 __device__ __forceinline__ void rect_mass_grad(const Guide& d, float dz[5]) {
     const float isx = d.il11, isy = rsqrtf(d.syy);
     const float rho = d.sxy * isx * isy;
     const float om = fmaf(-rho, rho, 1.0f), ir1 = rsqrtf(om);
     const float c0 = 0.398942280401432678f;      // 1 / sqrt(2 pi)
-    for (int k = 0; k < 5; ++k) dz[k] = 0.0f;
+    const float2 is = make_float2(isx, isy);
+    const float2 is2h = mul2(mul2(is, is), dup2(0.5f));
+    float2 dmu = dup2(0.0f), dsg = dup2(0.0f);
+    float dxy = 0.0f;
 #pragma unroll
     for (int cn = 0; cn < 4; ++cn) {
         const float a = (float)(cn & 1), b = (float)(cn >> 1);
         const float sg = (cn == 0 || cn == 3) ? 1.0f : -1.0f;
-        const float h = (a - d.mx) * isx, k = (b - d.my) * isy;
-        const float dh = c0 * __expf(-0.5f * h * h) * normal_cdf((k - rho * h) * ir1);
-        const float dk = c0 * __expf(-0.5f * k * k) * normal_cdf((h - rho * k) * ir1);
+        const float2 hk = mul2(make_float2(a - d.mx, b - d.my), is);          // (h, k)
+        const float2 kh = make_float2(hk.y, hk.x);
+        // (dPhi2/dh, dPhi2/dk) = phi(h) Phi((k - rho h)/sqrt(1 - rho^2)), and with h, k swapped
+        const float2 dhk = mul2(mul2(dup2(c0), exp2x(mul2(dup2(-0.5f), mul2(hk, hk)))),
+                                normal_cdf2(mul2(fma2(dup2(-rho), hk, kh), dup2(ir1))));
+        const float h = hk.x, k = hk.y;
         const float dr = kInv2Pi * ir1 * __expf(-0.5f * (h * h - 2.0f * rho * h * k + k * k) / om);
-        dz[0] -= sg * dh * isx;
-        dz[1] -= sg * dk * isy;
-        dz[2] -= sg * (dh * h + dr * rho) * 0.5f * isx * isx;
-        dz[3] -= sg * (dk * k + dr * rho) * 0.5f * isy * isy;
-        dz[4] += sg * dr * isx * isy;
+        dmu = fma2(dup2(-sg), mul2(dhk, is), dmu);
+        dsg = fma2(dup2(-sg), mul2(fma2(dhk, hk, dup2(dr * rho)), is2h), dsg);
+        dxy = fmaf(sg * dr, isx * isy, dxy);
     }
+    dz[0] = dmu.x;
+    dz[1] = dmu.y;
+    dz[2] = dsg.x;
+    dz[3] = dsg.y;
+    dz[4] = dxy;
 }
 
 // ---------------------------------------------------------------------------
 // Weighted online EM (Sec. 3.2). Statistics over BRDF-strategy draws only, in
-// binary32 with Kahan compensation, taken about the stored mean so the second
-// moments need no cancellation: a = sum w g, b = sum w, S1 = sum w g (u - E),
-// S2 = sum w g (u - E)(u - E)^T, with w = f / p_b the luminance weight of
-// the draw and g = pi p_g / p_mix its posterior for the guide.
+// binary32: the masses a = sum w g and b = sum w with Kahan compensation, and
+// the batch's weighted mean and second central moment by West's incremental
+// update (West 1979: each draw moves the mean by its weight's share of the
+// running mass and adds its share of the spread), with w = f / p_b the
+// luminance weight of the draw and g = pi p_g / p_mix its posterior for the
+// guide. Unlike sums of (u - c)(u - c)^T about a fixed point c, from which the
+// covariance follows only as a difference, no step of this update cancels,
+// however unequal the weights (a bright draw after a dim one at another place
+// leaves a batch covariance far below the square of their distance).
 // ---------------------------------------------------------------------------
 struct Kahan {
     float s = 0.0f, c = 0.0f;
@@ -1051,9 +1127,10 @@ struct Kahan2 {
 };
 
 struct Stats {
-    // (a, b), (S1x, S1y), (S2xx, S2yy) in pairs and S2xy alone
-    Kahan2 ab, s1, s2;
-    Kahan s2xy;
+    Kahan2 ab;          // (a, b)
+    float2 m = {0.0f, 0.0f};   // weighted mean of the batch's square coordinates (weights w g)
+    Kahan2 c2;          // weighted second central moments (M_xx, M_yy), times a
+    Kahan c2xy;         // M_xy times a
     bool empty = true;
     __device__ __forceinline__ void add_train(const Guide& d, const Gam& g, const Smp& o) {
         if (o.strat != ST_BRDF || !(o.pb > 0.0f)) return;
@@ -1088,24 +1165,27 @@ struct Stats {
         }
         add(g, w, gam, u.x, u.y);
     }
-    __device__ __forceinline__ void add(const Gam& g, float w, float gam, float ux, float uy) {
-        const float wg = w * gam;
-        const float2 d = sub2(make_float2(ux, uy), make_float2(g.ex, g.ey));
-        const float2 wd = mul2(dup2(wg), d);        // (wg dx, wg dy)
-        const float2 wdd = mul2(wd, d);             // (wg dx dx, wg dy dy)
-        const float wxy = wd.x * d.y;               // wg dx dy
+    __device__ __forceinline__ void add(const Gam&, float w, float gam, float ux, float uy) {
+        const float v = w * gam;
         if (empty) {
-            ab.set(make_float2(wg, w));
-            s1.set(wd);
-            s2.set(wdd);
-            s2xy.set(wxy);
+            ab.set(make_float2(v, w));
+            m = make_float2(ux, uy);
+            c2.set(dup2(0.0f));
+            c2xy.set(0.0f);
             empty = false;
             return;
         }
-        ab.add(make_float2(wg, w));
-        s1.add(wd);
-        s2.add(wdd);
-        s2xy.add(wxy);
+        const float a0 = ab.s.x;
+        ab.add(make_float2(v, w));
+        const float a1 = ab.s.x;
+        if (!(v > 0.0f) || !(a1 > 0.0f)) return;
+        // t = v / a1, the draw's share of the mass; f = v a0 / a1
+        const float t = fdiv(v, a1), f = t * a0;
+        const float2 d = sub2(make_float2(ux, uy), m);
+        m = fma2(d, dup2(t), m);
+        const float2 fd = mul2(dup2(f), d);
+        c2.add(mul2(fd, d));
+        c2xy.add(fd.x * d.y);
     }
 };
 
@@ -1114,11 +1194,18 @@ struct Stats {
 // carrying mass M0 = W (for an untrained guide, the frame's own mass b):
 //   A = (1-eta) pi M0 + eta a,  B = (1-eta) M0 + eta b,
 //   E <- ((1-eta) pi M0 E + eta S) / A,  pi <- clamp(A/B),  W <- B,  k <- k+1.
-// The moment update is applied about the stored mean: with lambda = eta a / A,
-// delta = S1/a and M2 = S2/a (batch offset and second moment about E[X]),
-//   mu' = mu + lambda delta,  Sigma' = (1-lambda) Sigma + lambda M2 - (lambda delta)(lambda delta)^T,
-// the same update in exact arithmetic, free of the cancellation of raw second
-// moments in binary32. A frame with b = 0 changes nothing.
+// The moments are updated as a mixture of the stored guide and the frame's
+// batch, with lambda = eta a / A and 1 - lambda = (1-eta) pi M0 / A:
+//   mu' = mu + lambda delta,
+//   Sigma' = (1-lambda) Sigma + lambda (C + (1-lambda) delta delta^T),
+// delta = the batch mean minus mu, C = the batch covariance about its own
+// mean. It is the same update in exact arithmetic, and every term of it is
+// free of cancellation in binary32, also as lambda -> 1 (a frame whose mass
+// dwarfs the stored guide's), where 1 - lambda formed as a difference, or
+// lambda M2 - (lambda delta)^2 from moments about mu, would lose the small
+// covariance that remains. ONE: at most one training sample (C = 0). A frame
+// with b = 0 changes nothing.
+template <bool ONE = false>
 __device__ __forceinline__ void m_step(const Params& P, Gam& g, const Stats& st) {
     const float k = fmaxf(g.k, 0.0f);
     const float a = st.ab.s.x, b = st.ab.s.y;
@@ -1131,29 +1218,38 @@ __device__ __forceinline__ void m_step(const Params& P, Gam& g, const Stats& st)
     const float A = fmaf(eta, a, keep);
     const float B = fmaf(eta, b, e1 * m0);
     if (a > 0.0f && A > 0.0f) {
-        // lambda delta = eta S1 / A and lambda M2 = eta S2 / A: bounded ratios,
-        // by one hardware reciprocal of A while A is normal (2 ulp, as fdiv's
-        // fast path), by correctly rounded divisions for a subnormal A
-        float lam, lmxy;
-        float2 ld, lm;          // (lambda dx, lambda dy), (lambda M2xx, lambda M2yy)
+        // lambda and 1 - lambda by one hardware reciprocal of A while A is
+        // normal (2 ulp, as fdiv's fast path), by correctly rounded divisions
+        // for a subnormal A; the same for C over a
+        float lam, l1, cxy = 0.0f;
+        float2 c = dup2(0.0f);
         if (A > 1e-30f) {
             const float rA = __fdividef(1.0f, A);
             lam = eta * a * rA;
-            ld = mul2(mul2(dup2(eta), st.s1.s), dup2(rA));
-            lm = mul2(mul2(dup2(eta), st.s2.s), dup2(rA));
-            lmxy = eta * st.s2xy.s * rA;
+            l1 = keep * rA;
         } else {
             lam = __fdiv_rn(eta * a, A);
-            ld = make_float2(__fdiv_rn(eta * st.s1.s.x, A), __fdiv_rn(eta * st.s1.s.y, A));
-            lm = make_float2(__fdiv_rn(eta * st.s2.s.x, A), __fdiv_rn(eta * st.s2.s.y, A));
-            lmxy = __fdiv_rn(eta * st.s2xy.s, A);
+            l1 = __fdiv_rn(keep, A);
         }
-        const float l1 = 1.0f - lam;
-        const float2 sd = fma2(dup2(l1), make_float2(g.sxx, g.syy), fma2(neg2(ld), ld, lm));
+        if (!ONE) {
+            if (a > 1e-30f) {
+                const float ra = __fdividef(1.0f, a);
+                c = mul2(st.c2.s, dup2(ra));
+                cxy = st.c2xy.s * ra;
+            } else {
+                c = make_float2(__fdiv_rn(st.c2.s.x, a), __fdiv_rn(st.c2.s.y, a));
+                cxy = __fdiv_rn(st.c2xy.s, a);
+            }
+        }
+        const float2 dl = sub2(st.m, make_float2(g.ex, g.ey));   // delta
+        const float2 l1d = mul2(dup2(l1), dl);
+        const float2 q = fma2(l1d, dl, c);             // C + (1 - lambda) delta delta^T
+        const float qxy = fmaf(l1d.x, dl.y, cxy);
+        const float2 sd = fma2(dup2(l1), make_float2(g.sxx, g.syy), mul2(dup2(lam), q));
         g.sxx = sd.x;
         g.syy = sd.y;
-        g.sxy = fmaf(l1, g.sxy, fmaf(-ld.x, ld.y, lmxy));
-        const float2 e = add2(make_float2(g.ex, g.ey), ld);
+        g.sxy = fmaf(l1, g.sxy, lam * qxy);
+        const float2 e = fma2(dup2(lam), dl, make_float2(g.ex, g.ey));
         g.ex = e.x;
         g.ey = e.y;
         raw_from_central(g);

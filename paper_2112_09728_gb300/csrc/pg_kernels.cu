@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const Params P, void* __restric
 // its code).
 // RGB: a coloured field; the image gets three planes [3][H*W].
 template <int DT, bool ONE, bool GLASS, bool RGB>
-__global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void* __restrict__ gin,
+__global__ void __launch_bounds__(kBlock, ONE ? 5 : 4) k_frame(const Params P, const void* __restrict__ gin,
                                                      void* __restrict__ gout, const float4* __restrict__ g0,
                                                      const float4* __restrict__ g1, const float4* __restrict__ g0p,
                                                      float* __restrict__ img, uint32_t frame, int* __restrict__ err) {
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_frame(const Params P, const void*
         }
         st.add_train(d, g, o);
     }
-    m_step(P, g, st);
+    m_step<ONE>(P, g, st);
     if (!gam_finite(g)) atomicOr(err, PG_ERR_BIT_NUMERIC);
     store_step<DT>(P, gout, hw, (size_t)i, g, frame);
     if (img) {

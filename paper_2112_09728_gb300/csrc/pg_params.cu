@@ -183,6 +183,13 @@ pg_status field_params(const pg_field* f, Params& P, std::string& why) {
             for (int c = 0; c < 3; ++c) P.lobe_rgb[j][c] = 0.0f;
         }
     }
+    for (int jp = 0; jp < 4; ++jp) {
+        const int a = 2 * jp, b = 2 * jp + 1;
+        P.lobe_pnx[jp] = make_float2(-P.lobe_dir[a][0], -P.lobe_dir[b][0]);
+        P.lobe_pny[jp] = make_float2(-P.lobe_dir[a][1], -P.lobe_dir[b][1]);
+        P.lobe_pnz[jp] = make_float2(-P.lobe_dir[a][2], -P.lobe_dir[b][2]);
+        P.lobe_pe2[jp] = make_float2(P.lobe_e2[a], P.lobe_e2[b]);
+    }
     P.field_const = f->rgb ? (float)lum(f->constant_rgb) : f->constant;
     for (int c = 0; c < 3; ++c) P.field_const_rgb[c] = f->rgb ? f->constant_rgb[c] : 0.0f;
     P.mask_kind = f->mask_kind;
