@@ -579,36 +579,36 @@ __device__ __forceinline__ float2 sin_small2(float2 t) {
 // max(h^2, k^2), and >= h^2 + k^2 when hk rho <= 0, a corner whose bound
 // exceeds 36 contributes below e^-18 (times asin(rho)/(2 pi) < 0.18) and is
 // skipped.
+// Every operation of Z is an explicitly rounded one (the paired intrinsics,
+// fmaf, __fmul_rn, __fadd_rn), none left to the compiler to contract, so
+// that every kernel (fused, staged, adjoint, reuse) computes the same Z bit
+// for bit from the same guide.
 __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, float isx, float isy, float rho) {
-    const float h0 = -mx * isx, h1 = (1.0f - mx) * isx;
-    const float k0 = -my * isy, k1 = (1.0f - my) * isy;
+    const float h0 = __fmul_rn(-mx, isx), h1 = __fmul_rn(__fsub_rn(1.0f, mx), isx);
+    const float k0 = __fmul_rn(-my, isy), k1 = __fmul_rn(__fsub_rn(1.0f, my), isy);
     // the tails of both axes in pairs: (T(-h0), T(-k0)) and (T(h1), T(k1))
     const float2 ta = normal_tail2(make_float2(-h0, -k0)), tb = normal_tail2(make_float2(h1, k1));
     const float2 dp = sub2(sub2(dup2(1.0f), ta), tb);
-    float z = dp.x * dp.y;
-    const float h0s = h0 * h0, h1s = h1 * h1, k0s = k0 * k0, k1s = k1 * k1;
+    float z = __fmul_rn(dp.x, dp.y);
+    const float h0s = __fmul_rn(h0, h0), h1s = __fmul_rn(h1, h1), k0s = __fmul_rn(k0, k0), k1s = __fmul_rn(k1, k1);
     // a corner contributes below e^-18 when its exponent bound exceeds 18:
     // (h^2 + k^2)/2 if h k rho <= 0 (the cross term only adds), else max(h^2, k^2)/2
     auto live = [&](float h, float k, float hs, float ks) {
-        const float bound = (h * k * rho <= 0.0f) ? hs + ks : fmaxf(hs, ks);
+        const float bound = (__fmul_rn(__fmul_rn(h, k), rho) <= 0.0f) ? __fadd_rn(hs, ks) : fmaxf(hs, ks);
         return bound <= 36.0f;
     };
     const bool c00 = live(h0, k0, h0s, k0s), c10 = live(h1, k0, h1s, k0s);
     const bool c01 = live(h0, k1, h0s, k1s), c11 = live(h1, k1, h1s, k1s);
     if (rho != 0.0f && (c00 || c10 || c01 || c11)) {
-        const float asr = asinf(rho), half = 0.5f * asr;
-        // exponent of corner (h, k) in base 2: (2hk s - h^2 - k^2) log2(e) / (2 cos^2 t);
-        // a skipped corner gets a = +inf, so that its terms are exactly 0
+        const float asr = asinf(rho), half = __fmul_rn(0.5f, asr);
+        // exponent of corner (h, k) in base 2: (2hk s - h^2 - k^2) log2(e) / (2 cos^2 t)
         const float l2 = 0.72134752044448170f;                  // log2(e) / 2
-        const float inf = __int_as_float(0x7f800000);
-        const float a00 = c00 ? (h0s + k0s) * l2 : inf, b00 = 2.0f * h0 * k0 * l2;
-        const float a11 = c11 ? (h1s + k1s) * l2 : inf, b11 = 2.0f * h1 * k1 * l2;
-        const float a10 = c10 ? (h1s + k0s) * l2 : inf, b10 = 2.0f * h1 * k0 * l2;
-        const float a01 = c01 ? (h0s + k1s) * l2 : inf, b01 = 2.0f * h0 * k1 * l2;
-        // a corner no lane of the warp needs is left out by the whole warp
-        const unsigned act = __activemask();
-        const bool w00 = __any_sync(act, c00), w11 = __any_sync(act, c11);
-        const bool w10 = __any_sync(act, c10), w01 = __any_sync(act, c01);
+        auto a_of = [&](float hs, float ks) { return __fmul_rn(__fadd_rn(hs, ks), l2); };
+        auto b_of = [&](float h, float k) { return __fmul_rn(__fmul_rn(__fmul_rn(2.0f, h), k), l2); };
+        const float a00 = a_of(h0s, k0s), b00 = b_of(h0, k0);
+        const float a11 = a_of(h1s, k1s), b11 = b_of(h1, k1);
+        const float a10 = a_of(h1s, k0s), b10 = b_of(h1, k0);
+        const float a01 = a_of(h0s, k1s), b01 = b_of(h0, k1);
         auto corner = [](float b, float a, float2 s, float2 q) {
             const float2 e = mul2(fma2(dup2(b), s, dup2(-a)), q);
             return make_float2(exp2_approx(e.x), exp2_approx(e.y));
@@ -622,14 +622,14 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
             const float2 om = fma2(neg2(s), s, dup2(1.0f));
             const float2 q = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));  // 1 / cos^2 t >= 1
             float2 v = dup2(0.0f);
-            if (w00) v = add2(v, corner(b00, a00, s, q));
-            if (w11) v = add2(v, corner(b11, a11, s, q));
-            if (w10) v = sub2(v, corner(b10, a10, s, q));
-            if (w01) v = sub2(v, corner(b01, a01, s, q));
+            if (c00) v = add2(v, corner(b00, a00, s, q));
+            if (c11) v = add2(v, corner(b11, a11, s, q));
+            if (c10) v = sub2(v, corner(b10, a10, s, q));
+            if (c01) v = sub2(v, corner(b01, a01, s, q));
             acc = fmaf(P.gl_w[i], v.x, acc);
             acc = fmaf(P.gl_w[i + 1], v.y, acc);
         }
-        z = fmaf(acc, half * kInv2Pi, z);
+        z = fmaf(acc, __fmul_rn(half, kInv2Pi), z);
     }
     return z;
 }

@@ -69,6 +69,23 @@ def test_binding_covers_every_declared_symbol(lib):
     assert _declared() <= set(_lib.exported_names())
 
 
+def test_ctypes_mirror_of_pg_config_follows_the_header():
+    """The binding's pg_config has the header's fields, in the header's
+    order, so every field lands where the library reads it."""
+    from paper_2112_09728_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "pg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\} pg_config;", src).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(None, 1)[1].split(","):
+            names.append(re.sub(r"\[.*\]", "", part).strip())
+    assert names == [f[0] for f in _lib.pg_config._fields_]
+
+
 def test_config_default_and_validation_without_gpu(lib):
     from paper_2112_09728_gb300 import _lib
     cfg = _lib.pg_config()
