@@ -702,9 +702,6 @@ __device__ __forceinline__ float dielectric_fresnel(float ci) {
     return 0.5f * (rs * rs + rp * rp);
 }
 
-__device__ __forceinline__ float smith_g1(float a2, float c) {
-    return __fdividef(2.0f * c, c + sqrt_approx(fmaf(1.0f - a2, c * c, a2)));
-}
 
 // GLASS = false compiles the transparent material out (its code is then
 // Lambertian, as without P.glass); the kernels that always support it pass
@@ -734,7 +731,11 @@ __device__ __forceinline__ Surf make_surf(const Params& P, int x, int y, float4 
     const float a = fmaxf(g1.z * g1.z, 1e-4f);
     s.a2 = a * a;
     s.albedo = g1.w;
-    s.go = s.wo.z > 0.0f ? fdiv(g1.w * smith_g1(s.a2, s.wo.z), 4.0f * s.wo.z) : 0.0f;
+    // albedo G1(w_o) / (4 cos_o) with Smith's G1(c) = 2c / (c + sqrt(a^2 + (1 - a^2) c^2)):
+    // the cosines cancel, leaving albedo / (2 (c + e)), e >= alpha >= 1e-4
+    s.go = s.wo.z > 0.0f
+               ? __fdividef(0.5f * g1.w, s.wo.z + sqrt_approx(fmaf(1.0f - s.a2, s.wo.z * s.wo.z, s.a2)))
+               : 0.0f;
     return s;
 }
 
@@ -1134,8 +1135,18 @@ struct Stats {
     bool empty = true;
     __device__ __forceinline__ void add_train(const Guide& d, const Gam& g, const Smp& o) {
         if (o.strat != ST_BRDF || !(o.pb > 0.0f)) return;
-        const float w = fdiv(o.fcos, o.pb);
-        const float gam = o.pmix > 0.0f ? fdiv(d.pi_eff * o.pg, o.pmix) : 0.0f;
+        // w = f / p_b and gamma = pi p_g / p_mix through one reciprocal of
+        // p_b p_mix (> 0: p_mix >= (1 - pi Z) p_b) while it is a normal number
+        const float den = o.pb * o.pmix;
+        float w, gam;
+        if (den > 1e-30f && den < 1e30f) {
+            const float r = __fdividef(1.0f, den);
+            w = o.fcos * o.pmix * r;
+            gam = d.pi_eff * o.pg * o.pb * r;
+        } else {
+            w = fdiv(o.fcos, o.pb);
+            gam = o.pmix > 0.0f ? fdiv(d.pi_eff * o.pg, o.pmix) : 0.0f;
+        }
         add(g, w, gam, o.ux, o.uy);
     }
     // One reused VPL (Sec. 3.2): world direction ww and radiance L of a
