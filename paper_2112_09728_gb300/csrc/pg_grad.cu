@@ -54,24 +54,27 @@ __global__ void __launch_bounds__(kBlock, 4) k_grad(const Params P, const void* 
     // plain binary32 sums: at most a few hundred draws of one pixel, whose
     // rounding (~n 2^-24 of the summed magnitudes) is far inside the
     // adjoint's 1e-3 parity bound; compensation cost ~5% of the kernel
-    float l = 0.0f, ax = 0.0f, ay = 0.0f, axx = 0.0f, ayy = 0.0f, axy = 0.0f, sg = 0.0f, sb = 0.0f;
+    // (x, y) components in pairs: a = sum cg Sigma^-1 d, aa = sum cg (Sigma^-1 d)^2
+    float l = 0.0f, axy = 0.0f, sg = 0.0f, sb = 0.0f;
+    float2 a = dup2(0.0f), aa = dup2(0.0f);
     for (int si = 0; si < n; ++si) {
         const Smp o = draw_sample(P, d, s, (uint32_t)i, frame, (uint32_t)si, 2u);
         if ((o.strat & ST_INVALID) || o.fcos == 0.0f || !(o.pmix > 0.0f)) continue;
         const float ip = fdiv(1.0f, o.pmix), f2ip2 = o.fcos * o.fcos * ip * ip;
         l += f2ip2;
         if (!guided) continue;
-        const float dx = o.ux - d.mx, dy = o.uy - d.my;
-        const float ix = fmaf(qxx, dx, -qxy * dy), iy = fmaf(qyy, dy, -qxy * dx);
+        const float2 dd = sub2(make_float2(o.ux, o.uy), make_float2(d.mx, d.my));
+        // Sigma^-1 d = (qxx dx - qxy dy, qyy dy - qxy dx)
+        const float2 id = fma2(make_float2(qxx, qyy), dd, mul2(dup2(-qxy), make_float2(dd.y, dd.x)));
         const float c = -f2ip2 * ip, cg = c * o.pg;
-        ax = fmaf(cg, ix, ax);
-        ay = fmaf(cg, iy, ay);
-        axx = fmaf(cg * ix, ix, axx);
-        ayy = fmaf(cg * iy, iy, ayy);
-        axy = fmaf(cg * ix, iy, axy);
+        const float2 cid = mul2(dup2(cg), id);
+        a = add2(a, cid);
+        aa = fma2(cid, id, aa);
+        axy = fmaf(cid.x, id.y, axy);
         sg += cg;
         sb = fmaf(c, o.pb, sb);
     }
+    const float ax = a.x, ay = a.y, axx = aa.x, ayy = aa.y;
     const float in = 1.0f / (float)n;
     loss[i] = l * in;
     float gs[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
