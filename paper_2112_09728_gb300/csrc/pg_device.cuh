@@ -873,32 +873,45 @@ __device__ __forceinline__ float occlusion_mask(float A, float B) {
     return neg ? 0.5f * fmaf(-v.x, v.y, v.x + v.y) : 0.5f * fmaf(1.0f - v.x, 1.0f - v.y, 1.0f);
 }
 
+// The first 2 NP lobes, two per paired operation (each half the scalar
+// operations of one lobe), summed in lobe order into s (and the channels).
+// A lobe beyond n_lobes has scale 0 and exponent 0: it adds exactly 0.
+template <int NP, bool RGB>
+__device__ __forceinline__ void lobe_sums(const Params& P, float3 w, float& s, float& sr, float& sg, float& sb) {
+    const float2 wx = dup2(w.x), wy = dup2(w.y), wz = dup2(w.z);
+#pragma unroll
+    for (int jp = 0; jp < NP; ++jp) {
+        const int j = 2 * jp;
+        const float2 dx = add2(wx, P.lobe_pnx[jp]), dy = add2(wy, P.lobe_pny[jp]), dz = add2(wz, P.lobe_pnz[jp]);
+        const float2 q = mul2(P.lobe_pe2[jp], fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))));
+        const float e0 = exp2_approx(q.x), e1 = exp2_approx(q.y);
+        s = fmaf(P.lobe_scale[j], e0, s);
+        s = fmaf(P.lobe_scale[j + 1], e1, s);
+        if (RGB) {
+            sr = fmaf(P.lobe_rgb[j][0], e0, sr);
+            sg = fmaf(P.lobe_rgb[j][1], e0, sg);
+            sb = fmaf(P.lobe_rgb[j][2], e0, sb);
+            sr = fmaf(P.lobe_rgb[j + 1][0], e1, sr);
+            sg = fmaf(P.lobe_rgb[j + 1][1], e1, sg);
+            sb = fmaf(P.lobe_rgb[j + 1][2], e1, sb);
+        }
+    }
+}
+
 // Returns the radiance's luminance (the field itself when monochrome); with
-// RGB, *rgb receives its three channels (coloured fields). The lobes go in
-// pairs (each half the scalar operations of one lobe), summed in lobe order.
+// RGB, *rgb receives its three channels (coloured fields). One branch on the
+// field's lobe count (the same for every lane) picks straight-line code for
+// 2, 4 or 8 lobes: a branch per lobe pair costs more than the pairs it skips
+// (measured: the 8-lobe 4K frame 5% faster without them).
 template <bool RGB = false>
 __device__ __forceinline__ float radiance(const Params& P, float3 pos, float3 w, float3* rgb = nullptr) {
     float s = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
-    const float2 wx = dup2(w.x), wy = dup2(w.y), wz = dup2(w.z);
-#pragma unroll
-    for (int jp = 0; jp < 4; ++jp) {
-        const int j = 2 * jp;
-        if (j < P.n_lobes) {
-            const float2 dx = add2(wx, P.lobe_pnx[jp]), dy = add2(wy, P.lobe_pny[jp]), dz = add2(wz, P.lobe_pnz[jp]);
-            const float2 q = mul2(P.lobe_pe2[jp], fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))));
-            const float e0 = exp2_approx(q.x), e1 = exp2_approx(q.y);
-            // a lobe beyond n_lobes has scale 0 and exponent 0: it adds exactly 0
-            s = fmaf(P.lobe_scale[j], e0, s);
-            s = fmaf(P.lobe_scale[j + 1], e1, s);
-            if (RGB) {
-                sr = fmaf(P.lobe_rgb[j][0], e0, sr);
-                sg = fmaf(P.lobe_rgb[j][1], e0, sg);
-                sb = fmaf(P.lobe_rgb[j][2], e0, sb);
-                sr = fmaf(P.lobe_rgb[j + 1][0], e1, sr);
-                sg = fmaf(P.lobe_rgb[j + 1][1], e1, sg);
-                sb = fmaf(P.lobe_rgb[j + 1][2], e1, sb);
-            }
-        }
+    if (P.n_lobes > 4) {
+        lobe_sums<4, RGB>(P, w, s, sr, sg, sb);
+    } else if (P.n_lobes > 2) {
+        lobe_sums<2, RGB>(P, w, s, sr, sg, sb);
+    } else if (P.n_lobes > 0) {
+        lobe_sums<1, RGB>(P, w, s, sr, sg, sb);
     }
     if (P.mask_kind == 1) {
         const float m = occlusion_mask(2.0f * (P.mask[0] * pos.x + P.mask[2] * w.x),
