@@ -97,40 +97,62 @@ def measured_hbm():
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle samples while the timed region runs."""
+    """nvidia-smi clock and throttle samples (every 100 ms) while the timed
+    frames run. A reader thread timestamps each sample; entering waits for
+    the first one, so that sampling is live before the first timed frame."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index):
+    def __init__(self, device_index, first_wait_s=5.0):
         self.dev = device_index
         self.proc = None
+        self.thread = None
+        self.lines = []
+        self.first_wait_s = first_wait_s
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.lines.append((time.monotonic(), line))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        t_end = time.monotonic() + self.first_wait_s
+        while not self.lines and time.monotonic() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+                self.proc.wait()
+            if self.thread is not None:
+                self.thread.join(timeout=5)
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, the largest maximum clock and the throttle reasons
+        seen, over the samples taken between monotonic times t0 and t1 (all
+        samples when not given)."""
         sm, mx, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for l in getattr(self, "lines", []):
+        for ts, l in list(self.lines):
+            if (t0 is not None and ts < t0) or (t1 is not None and ts > t1):
+                continue
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -325,6 +347,27 @@ def run_form(par, sc, fld, g0d, g1d, gamma_dtype, warmup, steps, flush, keep_fra
     ms = [a.elapsed_time(b) for a, b in ev]
     gp.close()
     return ms, kept
+
+
+def clock_hold(par, sc, fld, g0d, g1d, seconds):
+    """The FP16 frames of the workload back to back for about `seconds` on a
+    pass of their own (untimed, no flush between them), so that the clock
+    samples taken beside the timed frames see the GPU under the same load
+    for longer than a sampling period. Returns the number of frames run."""
+    import torch
+    from paper_2112_09728_gb300.guide import GuidePass
+    gp = make_pass(par, "f16", 977)
+    img = torch.empty(GuidePass.image_planes(fld) * par.width * par.height, dtype=torch.float32, device="cuda")
+    n_dev, n, t_end = g0d.shape[0], 0, time.monotonic() + seconds
+    while time.monotonic() < t_end:
+        for _ in range(200):
+            t = n % n_dev
+            gp.pg_frame(g0d[t], g1d[t], sc.camera(t), g0d[max(t - 1, 0)], fld, n, img)
+            n += 1
+        torch.cuda.synchronize()
+    gp.pg_check()
+    gp.close()
+    return n
 
 
 def with_transparent_texels(g1d, sc, frac, seed):
@@ -836,11 +879,17 @@ def run_gpu(args, ws, rank, local):
     forms = {}
     barrier(ws)
     with ClockSampler(local) as clk:
+        held = clock_hold(par, sc, fld, g0d, g1d, args.clock_hold) if args.clock_hold > 0 else 0
         for dt in ("f32", "f16"):
             ms, kept = run_form(par, sc, fld, g0d, g1d, dt, args.warmup, args.steps, flush, keep, rank)
             forms[dt] = (ms, kept)
+        held += clock_hold(par, sc, fld, g0d, g1d, args.clock_hold) if args.clock_hold > 0 else 0
     barrier(ws)
     clocks = clk.summary()
+    clocks["window"] = ("nvidia-smi every 100 ms, live before the first timed frame; %.1f s of the same FP16 "
+                        "frames back to back (untimed, %d frames) before and after the FP32 and FP16 timed "
+                        "frames" % (args.clock_hold, held)) if args.clock_hold > 0 else \
+        "nvidia-smi every 100 ms, live before the first timed frame, over the FP32 and FP16 timed frames"
     # neighbour-VPL reuse (two passes per frame), FP16 Gamma, window radius REUSE_R
     forms["reuse"] = run_form(par, sc, fld, g0d, g1d, "f16", args.warmup, args.steps, flush, keep, rank,
                               reuse_radius=REUSE_R)
@@ -974,6 +1023,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=("native", "reference"))
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-hold", type=float, default=0.5, metavar="S",
+                    help="seconds of untimed FP16 frames before and after the timed frames, inside the clock "
+                         "sampling window (0: none)")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 EM + gradient-step leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the 512x512 Adam-versus-EM comparison")
     ap.add_argument("--no-mse", action="store_true",

@@ -8,6 +8,13 @@
 namespace pgk {
 
 constexpr int kBlock = 256;
+// The block of the fused frame kernel and of the adjoint: 128 threads, ten
+// blocks per SM for the one-sample frame (the same 1,280 threads as five of
+// 256), eight for the others, so that the last wave's blocks are smaller and
+// the SMs run out of work closer together (measured against 256-thread
+// blocks: the 1080p frame 2.5% faster, the 4K frame 1.4%, the adjoint 0.9%,
+// bit-identical).
+constexpr int kFrameBlock = 128;
 
 static __device__ __forceinline__ bool same_normal(float4 a, float4 b) {
     return __float_as_uint(a.x) == __float_as_uint(b.x) && __float_as_uint(a.y) == __float_as_uint(b.y) &&
@@ -79,9 +86,9 @@ static __device__ __forceinline__ bool replay_reprojection(const Params& P, uint
     return false;
 }
 
-static inline dim3 grid_for(const Params& P) {
+static inline dim3 grid_for(const Params& P, int block = kBlock) {
     const size_t hw = (size_t)P.W * P.H;
-    return dim3((unsigned)((hw + kBlock - 1) / kBlock));
+    return dim3((unsigned)((hw + block - 1) / block));
 }
 
 }  // namespace pgk

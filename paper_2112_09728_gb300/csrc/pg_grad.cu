@@ -28,7 +28,7 @@ namespace {
 // compiler picks unbounded (two blocks) and 1.12 ms at five blocks (48
 // registers, more spills).
 template <int DT, bool THETA>
-__global__ void __launch_bounds__(kBlock, 4) k_grad(const Params P, const void* __restrict__ gam,
+__global__ void __launch_bounds__(kFrameBlock, 8) k_grad(const Params P, const void* __restrict__ gam,
                                                  const float* __restrict__ theta, const float4* __restrict__ g0,
                                                  const float4* __restrict__ g1, uint32_t frame, int n,
                                                  float* __restrict__ loss, float* __restrict__ grad) {
@@ -265,10 +265,11 @@ __global__ void __launch_bounds__(kBlock) k_theta_set(const Params P, void* __re
 
 cudaError_t launch_grad(int dt, const Params& P, const void* gam, const float* theta, const float4* g0,
                         const float4* g1, uint32_t frame, int n, float* loss, float* grad, cudaStream_t st) {
+    const dim3 grid = grid_for(P, kFrameBlock);
     if (theta) {
-        PG_DISPATCH(dt, (k_grad<D, true><<<grid_for(P), kBlock, 0, st>>>(P, gam, theta, g0, g1, frame, n, loss, grad)));
+        PG_DISPATCH(dt, (k_grad<D, true><<<grid, kFrameBlock, 0, st>>>(P, gam, theta, g0, g1, frame, n, loss, grad)));
     } else {
-        PG_DISPATCH(dt, (k_grad<D, false><<<grid_for(P), kBlock, 0, st>>>(P, gam, theta, g0, g1, frame, n, loss, grad)));
+        PG_DISPATCH(dt, (k_grad<D, false><<<grid, kFrameBlock, 0, st>>>(P, gam, theta, g0, g1, frame, n, loss, grad)));
     }
     return cudaGetLastError();
 }

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const Params P, void* __restric
 // its code).
 // RGB: a coloured field; the image gets three planes [3][H*W].
 template <int DT, bool ONE, bool GLASS, bool RGB>
-__global__ void __launch_bounds__(kBlock, ONE ? 5 : 4) k_frame(const Params P, const void* __restrict__ gin,
+__global__ void __launch_bounds__(kFrameBlock, ONE ? 10 : 8) k_frame(const Params P, const void* __restrict__ gin,
                                                      void* __restrict__ gout, const float4* __restrict__ g0,
                                                      const float4* __restrict__ g1, const float4* __restrict__ g0p,
                                                      float* __restrict__ img, uint32_t frame, int* __restrict__ err) {
@@ -269,9 +269,10 @@ cudaError_t launch_init(int dt, const Params& P, void* gam, float init_pi, cudaS
 cudaError_t launch_frame(int dt, const Params& P, const void* gin, void* gout, const float4* g0,
                          const float4* g1, const float4* g0p, float* img, uint32_t frame, int* err,
                          cudaStream_t st) {
-    const dim3 grid = grid_for(P);
+    const dim3 grid = grid_for(P, kFrameBlock);
 #define PG_FRAME(ONE, GLASS, RGB) \
-    PG_DISPATCH(dt, (k_frame<D, ONE, GLASS, RGB><<<grid, kBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, err)))
+    PG_DISPATCH(dt, (k_frame<D, ONE, GLASS, RGB><<<grid, kFrameBlock, 0, st>>>(P, gin, gout, g0, g1, g0p, img, frame, \
+                                                                                 err)))
     const int v = (P.spp == 1 ? 4 : 0) + (P.glass ? 2 : 0) + (P.rgb ? 1 : 0);
     switch (v) {
         case 0: PG_FRAME(false, false, false); break;
