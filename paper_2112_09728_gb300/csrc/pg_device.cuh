@@ -15,12 +15,14 @@ constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kInv2Pi = 0.159154943091895335769f;
 constexpr float kInv4Pi2 = 0.0253302959105844428f;   // 1 / (4 pi^2)
 constexpr float k4OverPi = 1.27323954473516268615f;
-// Gauss-Legendre nodes of the Phi_2 correction: one 8-node rule, whose
-// corner error stays near 1e-8 or below up to |rho| = 0.9, for every pixel.
-// (Fewer nodes would do for small |rho|, but pixels of one warp on different
-// rules run each rule's nodes in turn: on trained guides a warp then ran 11
-// to 14 node steps where one common rule runs 8.)
-constexpr int kGLNodes = 8;
+// Nodes of the Phi_2 correction: one 6-node rule fitted to the corner
+// integrals the kernels evaluate (fit_corner_rule.py), whose worst corner
+// error is 1.3e-8 up to |rho| = 0.9, about that of the 8-node
+// Gauss-Legendre rule (8e-9; the 6-node one's is 3.5e-7). One rule serves
+// every pixel: pixels of one warp on different rules would run each rule's
+// nodes in turn (on trained guides a warp then ran 11 to 14 node steps where
+// one common 8-node rule ran 8).
+constexpr int kZNodes = 6;
 
 enum { DT_F32 = 0, DT_F16 = 1, DT_BF16 = 2 };
 
@@ -69,8 +71,8 @@ struct Params {
     // channels (lobe_scale and field_const then hold the luminance)
     int rgb;
     float lobe_rgb[8][3], field_const_rgb[3];
-    // the Gauss-Legendre rule on [-1, 1] (computed on the host at context creation)
-    float gl_x[kGLNodes], gl_w[kGLNodes];
+    // the rule of Z's corner integrals: nodes and weights on [-1, 1]
+    float zq_x[kZNodes], zq_w[kZNodes];
     // neighbour-VPL reuse: window radius (0 = off), number of candidates
     // ((2R+1)^2 - 1) spp, and the stride of the walk through them
     int reuse_r, reuse_c, reuse_stride;
@@ -579,7 +581,7 @@ __device__ __forceinline__ float2 sin_small2(float2 t) {
 // Z by four corners of the bivariate normal cdf in the Drezner-Wesolowsky form
 //   Phi_2(h,k;rho) = Phi(h)Phi(k) + 1/(2 pi) int_0^asin(rho) exp(-(h^2+k^2-2hk sin t)/(2 cos^2 t)) dt,
 // so Z = (Phi(h1)-Phi(h0)) (Phi(k1)-Phi(k0)) + signed sum of the four corner
-// integrals, each by the 8-node Gauss-Legendre rule in t (abs. error ~1e-8
+// integrals, each by the fitted 6-node rule in t (abs. error below 1.3e-8
 // up to |rho| = 0.9). As (h^2+k^2-2hks)/cos^2 t >=
 // max(h^2, k^2), and >= h^2 + k^2 when hk rho <= 0, a corner whose bound
 // exceeds 36 contributes below e^-18 (times asin(rho)/(2 pi) < 0.18) and is
@@ -621,9 +623,9 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
         float acc = 0.0f;
         // two nodes at a time, each half of a pair one node
 #pragma unroll
-        for (int i = 0; i < kGLNodes; i += 2) {
+        for (int i = 0; i < kZNodes; i += 2) {
             const float2 hh = dup2(half);
-            const float2 s = sin_small2(fma2(hh, make_float2(P.gl_x[i], P.gl_x[i + 1]), hh));
+            const float2 s = sin_small2(fma2(hh, make_float2(P.zq_x[i], P.zq_x[i + 1]), hh));
             const float2 om = fma2(neg2(s), s, dup2(1.0f));
             const float2 q = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));  // 1 / cos^2 t >= 1
             float2 v = dup2(0.0f);
@@ -631,8 +633,8 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
             if (c11) v = add2(v, corner(b11, a11, s, q));
             if (c10) v = sub2(v, corner(b10, a10, s, q));
             if (c01) v = sub2(v, corner(b01, a01, s, q));
-            acc = fmaf(P.gl_w[i], v.x, acc);
-            acc = fmaf(P.gl_w[i + 1], v.y, acc);
+            acc = fmaf(P.zq_w[i], v.x, acc);
+            acc = fmaf(P.zq_w[i + 1], v.y, acc);
         }
         z = fmaf(acc, __fmul_rn(half, kInv2Pi), z);
     }

@@ -9,35 +9,13 @@ namespace pgk {
 
 namespace {
 
-// Gauss-Legendre rule on [-1, 1]: nodes are the roots of P_n found by Newton
-// iteration from Chebyshev-like starting points, weights 2/((1-x^2) P_n'(x)^2).
-void gauss_legendre(int n, float* x_out, float* w_out) {
-    for (int i = 0; i < n; ++i) {
-        double x = std::cos(M_PI * (i + 0.75) / (n + 0.5));
-        double dp = 0.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = x;
-            for (int k = 2; k <= n; ++k) {
-                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = n * (x * p1 - p0) / (x * x - 1.0);
-            const double dx = p1 / dp;
-            x -= dx;
-            if (std::fabs(dx) < 1e-16) break;
-        }
-        double p0 = 1.0, p1 = x;
-        for (int k = 2; k <= n; ++k) {
-            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-            p0 = p1;
-            p1 = p2;
-        }
-        dp = n * (x * p1 - p0) / (x * x - 1.0);
-        x_out[i] = (float)x;
-        w_out[i] = (float)(2.0 / ((1.0 - x * x) * dp * dp));
-    }
-}
+// The rule of Z's corner integrals on [-1, 1] (t = (T/2)(1 + x) on [0, T]),
+// six nodes fitted to the integrands the kernels evaluate by
+// fit_corner_rule.py, whose output these are.
+constexpr float kZRuleX[kZNodes] = {-8.955661129e-01f, -5.146598373e-01f, -2.415967388e-02f,
+                                    4.208293743e-01f, 7.538226449e-01f, 9.514929539e-01f};
+constexpr float kZRuleW[kZNodes] = {2.598020079e-01f, 4.685371647e-01f, 4.856380751e-01f,
+                                    3.943743677e-01f, 2.685023727e-01f, 1.231459021e-01f};
 
 }  // namespace
 
@@ -117,7 +95,10 @@ void config_params(const pg_config& cfg, Params& P) {
     P.init_c[0] = cfg.init_sigma[0];
     P.init_c[1] = cfg.init_sigma[1];
     P.init_c[2] = cfg.init_sigma[2];
-    gauss_legendre(pgk::kGLNodes, P.gl_x, P.gl_w);
+    for (int i = 0; i < kZNodes; ++i) {
+        P.zq_x[i] = kZRuleX[i];
+        P.zq_w[i] = kZRuleW[i];
+    }
     // neighbour reuse: C candidates, walked with the smallest stride >= 0.618 C
     // that is coprime with C (so N <= C picks are distinct)
     P.sr = cfg.stochastic_round;

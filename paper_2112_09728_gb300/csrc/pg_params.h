@@ -15,7 +15,7 @@ bool aligned16(const void* p);
 pg_status check_config(const pg_config* c, std::string& why);
 
 // The configuration part of the launch parameters (sizes, thresholds, the
-// re-initialised guide, the Philox key and the Gauss-Legendre rules).
+// re-initialised guide, the Philox key and the rule of Z's corner integrals).
 void config_params(const pg_config& cfg, Params& P);
 
 // The camera and the radiance-field parts; PG_ERR_ARG with a reason on a bad value.

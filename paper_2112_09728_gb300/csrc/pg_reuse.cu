@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_train(const Params P, const void*
     auto pb_at = [&](size_t q) { return TILED ? s_pb[q] : pb_src[q]; };
     auto vpl_at = [&](size_t q) { return TILED ? s_vpl[q] : vpl[q]; };
     const size_t n_slots = TILED ? (size_t)tn * spp : (size_t)spp * hw;
+    (void)n_slots;                               // read by the bounds-checked build only
     // candidate o: pixel cell o / spp of the window (p itself skipped), sample
     // o mod spp; the floor divisions are exact in binary32 for these small
     // integers. False for a cell off the screen.
