@@ -15,10 +15,10 @@ constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kInv2Pi = 0.159154943091895335769f;
 constexpr float kInv4Pi2 = 0.0253302959105844428f;   // 1 / (4 pi^2)
 constexpr float k4OverPi = 1.27323954473516268615f;
-// Nodes of the Phi_2 correction: one 6-node rule fitted to the corner
-// integrals the kernels evaluate (fit_corner_rule.py), whose worst corner
-// error is 1.3e-8 up to |rho| = 0.9, about that of the 8-node
-// Gauss-Legendre rule (8e-9; the 6-node one's is 3.5e-7). One rule serves
+// Nodes of the Phi_2 correction: one 6-node rule in s = sin t fitted to the
+// corner integrals the kernels evaluate (fit_corner_rule.py), whose worst
+// corner error is 1.3e-8 up to |rho| = 0.9, about that of the 8-node
+// Gauss-Legendre rule in t (8e-9; the 6-node one's is 3.5e-7). One rule serves
 // every pixel: pixels of one warp on different rules would run each rule's
 // nodes in turn (on trained guides a warp then ran 11 to 14 node steps where
 // one common 8-node rule ran 8).
@@ -71,8 +71,8 @@ struct Params {
     // channels (lobe_scale and field_const then hold the luminance)
     int rgb;
     float lobe_rgb[8][3], field_const_rgb[3];
-    // the rule of Z's corner integrals: nodes and weights on [-1, 1]
-    float zq_x[kZNodes], zq_w[kZNodes];
+    // the rule of Z's corner integrals on [0, rho]: nodes s = rho c, weights rho w
+    float zq_c[kZNodes], zq_w[kZNodes];
     // neighbour-VPL reuse: window radius (0 = off), number of candidates
     // ((2R+1)^2 - 1) spp, and the stride of the walk through them
     int reuse_r, reuse_c, reuse_stride;
@@ -509,19 +509,6 @@ struct Guide {
     float Z, pi_eff;
 };
 
-// sin t for |t| <= 1.2 by its Taylor series through t^13 (remainder below
-// 1.2e-11): the nodes of the Phi_2 rule never leave [-asin 0.9, asin 0.9].
-__device__ __forceinline__ float sin_small(float t) {
-    const float t2 = t * t;
-    float p = 1.6059043836821613e-10f;           //  1/13!
-    p = fmaf(p, t2, -2.5052108385441720e-8f);    // -1/11!
-    p = fmaf(p, t2, 2.7557319223985891e-6f);     //  1/9!
-    p = fmaf(p, t2, -1.9841269841269841e-4f);    // -1/7!
-    p = fmaf(p, t2, 8.3333333333333333e-3f);     //  1/5!
-    p = fmaf(p, t2, -1.6666666666666667e-1f);    // -1/3!
-    return fmaf(t * t2, p, t);
-}
-
 // Upper tail 1 - Phi(h) = erfc(h / sqrt 2) / 2 for h >= 0; below 8e-9 past
 // h = 5.66, where it is dropped. erfc(x) ~ t exp(-x^2 + Q(t - 0.66)) with
 // t = 1 / (1 + x/2) and Q of degree 9, fitted by this library
@@ -566,23 +553,12 @@ __device__ __forceinline__ float2 normal_tail2(float2 h) {
     return make_float2(h.x < 5.66f ? v.x : 0.0f, h.y < 5.66f ? v.y : 0.0f);
 }
 
-// sin_small of two arguments at once.
-__device__ __forceinline__ float2 sin_small2(float2 t) {
-    const float2 t2 = mul2(t, t);
-    float2 p = dup2(1.6059043836821613e-10f);
-    p = fma2(p, t2, dup2(-2.5052108385441720e-8f));
-    p = fma2(p, t2, dup2(2.7557319223985891e-6f));
-    p = fma2(p, t2, dup2(-1.9841269841269841e-4f));
-    p = fma2(p, t2, dup2(8.3333333333333333e-3f));
-    p = fma2(p, t2, dup2(-1.6666666666666667e-1f));
-    return fma2(mul2(t, t2), p, t);
-}
-
 // Z by four corners of the bivariate normal cdf in the Drezner-Wesolowsky form
 //   Phi_2(h,k;rho) = Phi(h)Phi(k) + 1/(2 pi) int_0^asin(rho) exp(-(h^2+k^2-2hk sin t)/(2 cos^2 t)) dt,
 // so Z = (Phi(h1)-Phi(h0)) (Phi(k1)-Phi(k0)) + signed sum of the four corner
-// integrals, each by the fitted 6-node rule in t (abs. error below 1.3e-8
-// up to |rho| = 0.9). As (h^2+k^2-2hks)/cos^2 t >=
+// integrals, each by the fitted 6-node rule in s = sin t on [0, rho] (abs.
+// error below 1.4e-8 up to |rho| = 0.9; dt = ds / cos t, cos^2 t = 1 - s^2,
+// so a node needs no sine and rho no arcsine). As (h^2+k^2-2hks)/cos^2 t >=
 // max(h^2, k^2), and >= h^2 + k^2 when hk rho <= 0, a corner whose bound
 // exceeds 36 contributes below e^-18 (times asin(rho)/(2 pi) < 0.18) and is
 // skipped.
@@ -607,7 +583,6 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
     const bool c00 = live(h0, k0, h0s, k0s), c10 = live(h1, k0, h1s, k0s);
     const bool c01 = live(h0, k1, h0s, k1s), c11 = live(h1, k1, h1s, k1s);
     if (rho != 0.0f && (c00 || c10 || c01 || c11)) {
-        const float asr = asinf(rho), half = __fmul_rn(0.5f, asr);
         // exponent of corner (h, k) in base 2: (2hk s - h^2 - k^2) log2(e) / (2 cos^2 t)
         const float l2 = 0.72134752044448170f;                  // log2(e) / 2
         auto a_of = [&](float hs, float ks) { return __fmul_rn(__fadd_rn(hs, ks), l2); };
@@ -621,22 +596,23 @@ __device__ __forceinline__ float rect_mass(const Params& P, float mx, float my, 
             return make_float2(exp2_approx(e.x), exp2_approx(e.y));
         };
         float acc = 0.0f;
-        // two nodes at a time, each half of a pair one node
+        // two nodes at a time, each half of a pair one node: s = rho c,
+        // cos^2 t = 1 - s^2 >= 0.19, q = 1 / cos^2 t, the weight w / cos t
 #pragma unroll
         for (int i = 0; i < kZNodes; i += 2) {
-            const float2 hh = dup2(half);
-            const float2 s = sin_small2(fma2(hh, make_float2(P.zq_x[i], P.zq_x[i + 1]), hh));
+            const float2 s = mul2(dup2(rho), make_float2(P.zq_c[i], P.zq_c[i + 1]));
             const float2 om = fma2(neg2(s), s, dup2(1.0f));
-            const float2 q = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));  // 1 / cos^2 t >= 1
+            const float2 q = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+            const float2 wr = mul2(make_float2(P.zq_w[i], P.zq_w[i + 1]), make_float2(rsqrtf(om.x), rsqrtf(om.y)));
             float2 v = dup2(0.0f);
             if (c00) v = add2(v, corner(b00, a00, s, q));
             if (c11) v = add2(v, corner(b11, a11, s, q));
             if (c10) v = sub2(v, corner(b10, a10, s, q));
             if (c01) v = sub2(v, corner(b01, a01, s, q));
-            acc = fmaf(P.zq_w[i], v.x, acc);
-            acc = fmaf(P.zq_w[i + 1], v.y, acc);
+            acc = fmaf(wr.x, v.x, acc);
+            acc = fmaf(wr.y, v.y, acc);
         }
-        z = fmaf(acc, __fmul_rn(half, kInv2Pi), z);
+        z = fmaf(acc, __fmul_rn(rho, kInv2Pi), z);
     }
     return z;
 }

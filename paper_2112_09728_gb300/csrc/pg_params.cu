@@ -9,13 +9,13 @@ namespace pgk {
 
 namespace {
 
-// The rule of Z's corner integrals on [-1, 1] (t = (T/2)(1 + x) on [0, T]),
-// six nodes fitted to the integrands the kernels evaluate by
+// The rule of Z's corner integrals on [0, rho] in s = sin t (nodes rho c,
+// weights rho w), six nodes fitted to the integrands the kernels evaluate by
 // fit_corner_rule.py, whose output these are.
-constexpr float kZRuleX[kZNodes] = {-8.955661129e-01f, -5.146598373e-01f, -2.415967388e-02f,
-                                    4.208293743e-01f, 7.538226449e-01f, 9.514929539e-01f};
-constexpr float kZRuleW[kZNodes] = {2.598020079e-01f, 4.685371647e-01f, 4.856380751e-01f,
-                                    3.943743677e-01f, 2.685023727e-01f, 1.231459021e-01f};
+constexpr float kZRuleC[kZNodes] = {6.453754298e-02f, 2.967437484e-01f, 5.753261929e-01f,
+                                    7.920209216e-01f, 9.232052864e-01f, 9.863174196e-01f};
+constexpr float kZRuleW[kZNodes] = {1.604145295e-01f, 2.797993463e-01f, 2.581585785e-01f,
+                                    1.724387613e-01f, 9.353107058e-02f, 3.565772626e-02f};
 
 }  // namespace
 
@@ -96,7 +96,7 @@ void config_params(const pg_config& cfg, Params& P) {
     P.init_c[1] = cfg.init_sigma[1];
     P.init_c[2] = cfg.init_sigma[2];
     for (int i = 0; i < kZNodes; ++i) {
-        P.zq_x[i] = kZRuleX[i];
+        P.zq_c[i] = kZRuleC[i];
         P.zq_w[i] = kZRuleW[i];
     }
     // neighbour reuse: C candidates, walked with the smallest stride >= 0.618 C

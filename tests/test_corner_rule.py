@@ -1,12 +1,14 @@
 """The kernels' rule for Z's corner integrals (the table in pg_params.cu,
 fitted by fit_corner_rule.py). Each corner of Z adds the Drezner-Wesolowsky
 correction I(h, k, rho) = 1/(2 pi) int_0^asin(rho) exp(-(h^2 + k^2 - 2 h k
-sin t) / (2 cos^2 t)) dt to Phi(h) Phi(k); the rule must integrate it, for
-every corner the kernels evaluate, about as well as the 8-node
-Gauss-Legendre rule it replaced. Checked in binary64 against a 300-node
-Gauss-Legendre value on a seeded sample of live corners (another sample than
-the fit's), and against Phi_2 itself through Owen's T function at a few
-points, so that a wrong node, weight or sign in the table fails."""
+sin t) / (2 cos^2 t)) dt to Phi(h) Phi(k), which the kernels take in s = sin t
+on [0, rho] (dt = ds / sqrt(1 - s^2)) at nodes s = rho c with weights rho w;
+the rule must integrate it, for every corner the kernels evaluate, about as
+well as the 8-node Gauss-Legendre rule in t it replaced. Checked in binary64
+against a 300-node Gauss-Legendre value in t on a seeded sample of live
+corners (another sample than the fit's), and against Phi_2 itself through
+Owen's T function at a few points, so that a wrong node, weight or sign in
+the table fails."""
 import os
 import re
 
@@ -19,7 +21,7 @@ CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 def _table():
     src = open(os.path.join(CSRC, "pg_params.cu")).read()
     out = []
-    for name in ("kZRuleX", "kZRuleW"):
+    for name in ("kZRuleC", "kZRuleW"):
         body = re.search(name + r"\[kZNodes\]\s*=\s*\{([^}]*)\}", src).group(1)
         out.append(np.array([float(v.strip().rstrip("f")) for v in body.split(",") if v.strip()]))
     n = int(re.search(r"constexpr int kZNodes = (\d+);", open(os.path.join(CSRC, "pg_device.cuh")).read()).group(1))
@@ -39,8 +41,8 @@ def _live_corners(seed, n):
     return h[keep][:n], k[keep][:n], r[keep][:n]
 
 
-def _rule(h, k, r, x, w):
-    """(T/2) sum w_i f((T/2)(1 + x_i)) / (2 pi), T = asin(rho), as the kernels take it."""
+def _in_t(h, k, r, x, w):
+    """A rule in t on [0, asin(rho)] given on [-1, 1] (nodes x, weights w)."""
     half = 0.5 * np.arcsin(r)
     t = half[:, None] * (1.0 + x[None, :])
     f = np.exp(-(h[:, None] ** 2 + k[:, None] ** 2 - 2.0 * h[:, None] * k[:, None] * np.sin(t))
@@ -48,23 +50,34 @@ def _rule(h, k, r, x, w):
     return half * (f @ w) / (2.0 * np.pi)
 
 
-def test_rule_is_on_the_interval_and_integrates_constants():
-    x, w = _table()
-    assert np.all(np.diff(x) > 0) and x[0] > -1.0 and x[-1] < 1.0
+def _rule(h, k, r, c, w):
+    """The kernels' form: rho/(2 pi) sum w_i f(rho c_i) / sqrt(1 - (rho c_i)^2)."""
+    s = r[:, None] * c[None, :]
+    om = 1.0 - s * s
+    f = np.exp(-(h[:, None] ** 2 + k[:, None] ** 2 - 2.0 * h[:, None] * k[:, None] * s) / (2.0 * om)) / np.sqrt(om)
+    return r * (f @ w) / (2.0 * np.pi)
+
+
+def test_rule_is_on_the_interval_and_integrates_the_arc():
+    c, w = _table()
+    assert np.all(np.diff(c) > 0) and c[0] > 0.0 and c[-1] < 1.0
     assert np.all(w > 0)
-    assert abs(w.sum() - 2.0) < 1e-6
+    # h = k = 0: the integrand in t is 1, the integral asin(rho) / (2 pi)
+    r = np.linspace(-0.9, 0.9, 181)
+    z = np.zeros_like(r)
+    assert np.abs(_rule(z, z, r, c, w) - np.arcsin(r) / (2.0 * np.pi)).max() < 1.4e-8
 
 
 def test_rule_matches_the_corner_integrals_within_the_replaced_rules_error():
-    x, w = _table()
+    c, w = _table()
     h, k, r = _live_corners(2024, 40000)
     xr, wr = np.polynomial.legendre.leggauss(300)
-    ref = _rule(h, k, r, xr, wr)
-    err = np.abs(_rule(h, k, r, x, w) - ref)
+    ref = _in_t(h, k, r, xr, wr)
+    err = np.abs(_rule(h, k, r, c, w) - ref)
     x8, w8 = np.polynomial.legendre.leggauss(8)
-    x6, w6 = np.polynomial.legendre.leggauss(len(x))
-    err8 = np.abs(_rule(h, k, r, x8, w8) - ref).max()
-    err6 = np.abs(_rule(h, k, r, x6, w6) - ref).max()
+    x6, w6 = np.polynomial.legendre.leggauss(len(c))
+    err8 = np.abs(_in_t(h, k, r, x8, w8) - ref).max()
+    err6 = np.abs(_in_t(h, k, r, x6, w6) - ref).max()
     assert err.max() < 1.6e-8, err.max()
     assert err.max() < 2.0 * err8 and err.max() < err6 / 20.0
 
@@ -73,7 +86,7 @@ def test_rule_gives_phi2_through_owens_t():
     """Phi_2(h, k; rho) = Phi(h) Phi(k) + I(h, k, rho) against the textbook
     Owen's T form (scipy's owens_t), at points spread over the live range."""
     sp = pytest.importorskip("scipy.special")
-    x, w = _table()
+    c, w = _table()
     Phi = lambda v: 0.5 * sp.erfc(-v / np.sqrt(2.0))
 
     def phi2_owen(h, k, r):
@@ -88,5 +101,5 @@ def test_rule_gives_phi2_through_owens_t():
     pts = [(0.3, 0.7, 0.5), (-1.2, 0.4, -0.8), (2.0, 1.5, 0.9), (-0.65, 0.76, 0.9), (0.7, -0.9, 0.9),
            (3.0, -2.5, -0.6), (-4.0, -3.5, 0.85), (1.1, 1.1, -0.9), (0.05, -0.2, 0.3), (5.5, 5.0, 0.9)]
     for h, k, r in pts:
-        got = Phi(h) * Phi(k) + _rule(np.array([h]), np.array([k]), np.array([r]), x, w)[0]
+        got = Phi(h) * Phi(k) + _rule(np.array([h]), np.array([k]), np.array([r]), c, w)[0]
         assert abs(got - phi2_owen(h, k, r)) < 2e-8, (h, k, r, got, phi2_owen(h, k, r))
