@@ -33,13 +33,21 @@ template <int DT>
 static __device__ __forceinline__ bool reproject_pixel(const Params& P, int x, int y, float4 a0, float4 a1,
                                                 const void* __restrict__ gin, const float4* __restrict__ g0p,
                                                 size_t hw, Gam& g, int* err) {
-    float4 gp;
-    const int j = reproject_index(P, x, y, a0, a1, g0p, &gp, err);
+    const int j = reproject_target(P, x, y, a1, err);
     if (j < 0) {
         g = init_gam(P);
         return true;
     }
-    g = Store<DT>::load(gin, hw, (size_t)j);
+    // Gamma(t-1) at the target is loaded beside the previous G-buffer, before
+    // the test decides on it: the two loads overlap instead of following one
+    // another (for a rejected pixel the guide read goes unused)
+    const float4 gp = __ldcs(g0p + j);
+    const Gam gj = Store<DT>::load(gin, hw, (size_t)j);
+    if (!reproject_accept(P, a0, gp)) {
+        g = init_gam(P);
+        return true;
+    }
+    g = gj;
     if (!same_normal(gp, a0)) change_frame(g, make_float3(gp.x, gp.y, gp.z), make_float3(a0.x, a0.y, a0.z));
     return false;
 }
@@ -51,14 +59,19 @@ template <int DT>
 static __device__ __forceinline__ bool reproject_pixel_rec(const Params& P, int x, int y, float4 a0, float4 a1,
                                                     const void* __restrict__ gin, const float4* __restrict__ g0p,
                                                     size_t hw, Gam& g, uint32_t& rec, int* err) {
-    float4 gp;
-    const int j = reproject_index(P, x, y, a0, a1, g0p, &gp, err);
+    const int j = reproject_target(P, x, y, a1, err);
     rec = 0xFFFFFFFFu;
     if (j < 0) {
         g = init_gam(P);
         return true;
     }
-    g = Store<DT>::load(gin, hw, (size_t)j);
+    const float4 gp = __ldcs(g0p + j);
+    const Gam gj = Store<DT>::load(gin, hw, (size_t)j);   // beside the G-buffer load, as above
+    if (!reproject_accept(P, a0, gp)) {
+        g = init_gam(P);
+        return true;
+    }
+    g = gj;
     rec = (uint32_t)j;
     if (!same_normal(gp, a0)) {
         change_frame(g, make_float3(gp.x, gp.y, gp.z), make_float3(a0.x, a0.y, a0.z));

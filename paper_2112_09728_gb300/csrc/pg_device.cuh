@@ -458,20 +458,33 @@ __device__ __forceinline__ bool gam_finite(const Gam& g) {
 // order (no contraction), so the decision is reproducible bit for bit.
 // Returns the linear index of the previous pixel, or -1 for a rejection.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int reproject_index(const Params& P, int x, int y, float4 g0, float4 g1,
-                                               const float4* __restrict__ g0_prev, float4* g0p_out, int* err) {
+// The motion-compensated previous pixel of (x, y), or -1 off the screen.
+__device__ __forceinline__ int reproject_target(const Params& P, int x, int y, float4 g1, int* err) {
     const float fx = __fadd_rn(__fadd_rn((float)x, 0.5f), g1.x);
     const float fy = __fadd_rn(__fadd_rn((float)y, 0.5f), g1.y);
     if (!(fx >= 0.0f && fx < (float)P.W && fy >= 0.0f && fy < (float)P.H)) return -1;
     const int qx = (int)floorf(fx), qy = (int)floorf(fy);
     const int j = qy * P.W + qx;
     if (!PG_IN_BOUNDS(j, (long long)P.W * P.H, err)) return -1;
-    const float4 gp = __ldcs(g0_prev + j);
-    *g0p_out = gp;
+    return j;
+}
+
+// The depth and normal test between the current surface g0 and the previous
+// surface gp at the target pixel.
+__device__ __forceinline__ bool reproject_accept(const Params& P, float4 g0, float4 gp) {
     const float dd = fabsf(__fsub_rn(gp.w, g0.w));
     const float dl = __fmul_rn(P.depth_tol, g0.w);
     const float nd = __fadd_rn(__fadd_rn(__fmul_rn(gp.x, g0.x), __fmul_rn(gp.y, g0.y)), __fmul_rn(gp.z, g0.z));
-    return (dd <= dl && nd >= P.normal_tol) ? j : -1;
+    return dd <= dl && nd >= P.normal_tol;
+}
+
+__device__ __forceinline__ int reproject_index(const Params& P, int x, int y, float4 g0, float4 g1,
+                                               const float4* __restrict__ g0_prev, float4* g0p_out, int* err) {
+    const int j = reproject_target(P, x, y, g1, err);
+    if (j < 0) return -1;
+    const float4 gp = __ldcs(g0_prev + j);
+    *g0p_out = gp;
+    return reproject_accept(P, g0, gp) ? j : -1;
 }
 
 // Frame change between the previous and the current surface (Sec. 3.1): the
