@@ -23,10 +23,12 @@ namespace {
 //   dl/dpi    ~ sum cg - Z sum c p_b,
 // eight binary32 sums (the loss, five of cg times a monomial of Sigma^-1 d,
 // sum cg and sum c p_b); dZ/dtheta is taken once, after the loop.
-// Four blocks of 256 per SM (64 registers, 8 bytes spilled): 0.91 ms for the
-// 3840x2160 orbit step at 4 draws, against 1.21 ms at the register count the
-// compiler picks unbounded (two blocks) and 1.12 ms at five blocks (48
-// registers, more spills).
+// Eight blocks of 128 threads per SM (64 registers, no spills): 0.69 ms for
+// the 3840x2160 orbit step at 4 draws. When the bound was chosen, the
+// register count the compiler picks unbounded (two blocks of 256 per SM) ran
+// a third slower, and five blocks of 256 (48 registers, more spills) a
+// quarter slower, than four blocks of 256 with these 64 registers; blocks of
+// 128 then gained 1% over blocks of 256 (a smaller last wave).
 template <int DT, bool THETA>
 __global__ void __launch_bounds__(kFrameBlock, 8) k_grad(const Params P, const void* __restrict__ gam,
                                                  const float* __restrict__ theta, const float4* __restrict__ g0,
